@@ -1,0 +1,448 @@
+"""Benchmark of the fused BGK collide-and-stream path on GB300.
+
+Default workload: the D3Q19 lid-driven cavity 128^3 (halfway bounce-back on five
+walls, moving lid u = 0.05 on the whole top plane, Re = 400 through tau with
+L = 126, rho = 1, u = 0 plus seeded 1e-6 uniform population noise), FP32
+populations, 2000 collide-and-stream steps.  One bench step = the whole workload:
+equilibrium initialisation from the resident input fields, 2000 steps, and the
+lattice statistics of the last collision (fused into its kernel).
+
+Metric: MLUPS (million fluid-cell updates per second), with the HBM roofline of
+the step kernel (152 algorithmic bytes per fluid-cell update in FP32: 19
+populations read once and written once).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-variants]
+
+--impl reference times the FP64 CPU oracle (the plain reference implementation of
+the same map) on the host cores on a bounded sample of the same workload.
+Under torchrun (N > 1) each rank runs an independent replica on its own GPU
+(the path has no exchange step on one lattice per GPU); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2307_11752_gb300 import inputs as I  # noqa: E402
+
+N_SIDE = 128
+LBM_STEPS = 2000
+LID = 0.05
+TAU = I.cavity_tau(N_SIDE, 400.0, LID)
+SEED = 1
+METRIC = "MLUPS"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+
+
+def workload_config():
+    return {"workload": f"D3Q19 BGK lid-driven cavity {N_SIDE}^3, halfway bounce-back on 5 walls, "
+                        f"moving lid u={LID}, Re=400 (tau={TAU:.6f}, L={N_SIDE - 2}), rho=1 u=0 + "
+                        f"1e-6 seeded population noise, {LBM_STEPS} steps per bench step",
+            "lattice": "D3Q19", "cells": N_SIDE ** 3, "fluid_cells": (N_SIDE - 2) ** 3,
+            "lbm_steps_per_step": LBM_STEPS, "storage": "f32", "scheme": None,
+            "l2_policy": "inputs larger than L2: two 159 MB population buffers + 2 MB material per "
+                         "LBM step (318 MB streamed per step vs 129 MB L2)"}
+
+
+# --------------------------------------------------------------------------------------
+# distributed plumbing
+# --------------------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for rel in ("paper_2307_11752_gb300/csrc/olb_kernels.cuh",):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key: str, units: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, scaled
+    to `units` fluid cells; None when the kernel source changed since the capture."""
+    try:
+        with open(PROFILE_TRAFFIC) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    entry = rec.get(kernel_key)
+    if not entry or entry.get("source_sha") != kernel_source_sha():
+        return None
+    return float(entry["dram_bytes_per_fluid_cell"]) * units
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+def make_cavity(olb, torch, dtype="f32", scheme="pull", n=N_SIDE):
+    m = I.cavity(n)
+    lat = olb.Lattice(olb.D3Q19, (n, n, n), dtype=dtype, scheme=scheme)
+    lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 0)
+    lat.set_wall_velocity(I.LID, (LID, 0.0, 0.0))
+    lat.set_bgk(I.cavity_tau(n, 400.0, LID))
+    noise = torch.from_numpy(I.population_noise(SEED, 19, m, 1e-6).reshape(-1)).cuda()
+    return lat, m, noise
+
+
+def run_workload(lat, noise, steps=LBM_STEPS):
+    lat.init_equilibrium()
+    lat.perturb(noise)
+    return lat.step_stats(steps)
+
+
+def time_device(torch, lat, noise, K, W, steps=LBM_STEPS, flush=None):
+    for _ in range(W):
+        run_workload(lat, noise, steps)
+    torch.cuda.synchronize()
+    t0, k0 = lat.counters()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(lat.stream)
+    for _ in range(K):
+        stats = run_workload(lat, noise, steps)
+    end.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    t1, k1 = lat.counters()
+    return ms, k1 - k0, stats
+
+
+def time_step_kernel(torch, lat, steps):
+    """Average duration of the step kernel alone: CUDA events around `steps`
+    back-to-back olb_step launches on the lattice's stream."""
+    lat.step(4)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(lat.stream)
+    lat.step(steps)
+    end.record(lat.stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / steps
+
+
+def e2e_run(olb, torch, m, K):
+    """Same workload through the C ABI with host (pinned) buffers: the initial
+    fields go host -> device inside every step, the moments come back to the host."""
+    n = N_SIDE
+    lat = olb.Lattice(olb.D3Q19, (n, n, n), dtype="f32", scheme="pull")
+    lat.set_material(np.ascontiguousarray(m.reshape(-1)), 0)
+    lat.set_wall_velocity(I.LID, (LID, 0.0, 0.0))
+    lat.set_bgk(TAU)
+    cells = n ** 3
+    rho_h = torch.ones(cells, dtype=torch.float64).pin_memory()
+    u_h = torch.zeros(3 * cells, dtype=torch.float64).pin_memory()
+    noise_h = torch.from_numpy(I.population_noise(SEED, 19, m, 1e-6).reshape(-1)).pin_memory()
+    rho_o = torch.empty(cells, dtype=torch.float64).pin_memory()
+    u_o = torch.empty(3 * cells, dtype=torch.float64).pin_memory()
+
+    def one():
+        lat.init_equilibrium(rho_h, u_h)
+        lat.perturb(noise_h)
+        lat.step(LBM_STEPS)
+        lat.moments(rho_o, u_o)
+
+    one()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(K):
+        one()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t
+    h2d = (rho_h.numel() + u_h.numel() + noise_h.numel()) * 8
+    d2h = (rho_o.numel() + u_o.numel()) * 8
+    lat.close()
+    return sec, h2d, d2h
+
+
+def variants(olb, torch):
+    """Short measurements of the other storage types, the AA pattern, the 3D
+    Taylor-Green vortex at 512^3 and the adjoint (channel 256x128x128)."""
+    out = {}
+    peak, _ = measured_peak_gbs()
+    fluid = (N_SIDE - 2) ** 3
+    for dtype, scheme in (("f32", "aa"), ("f16", "pull"), ("f16", "aa"), ("bf16", "pull"),
+                          ("f64", "pull")):
+        lat, m, noise = make_cavity(olb, torch, dtype, scheme)
+        run_workload(lat, noise, 200)
+        ms = time_step_kernel(torch, lat, 400)
+        b = 19 * 2 * olb.STATE_ELEM[olb.DTYPES[dtype]]
+        out[f"cavity128_{dtype}_{scheme}"] = {
+            "MLUPS": round(fluid / ms / 1e3, 1), "bytes_per_update": b,
+            "roofline_frac": round(fluid * b / (ms * 1e-3) / 1e9 / peak, 4)}
+        lat.close()
+    # 3D Taylor-Green vortex 512^3, periodic (no wall cells)
+    n = 512
+    for dtype in ("f32", "f16"):
+        lat = olb.Lattice(olb.D3Q19, (n, n, n), dtype=dtype, scheme="pull")
+        lat.set_material(torch.ones(n ** 3, dtype=torch.uint8, device="cuda"), 7)
+        lat.set_bgk(0.6)
+        rho, u = I.tgv3d(n, 0.02, xp=torch, device="cuda")
+        lat.init_equilibrium(rho.reshape(-1), u.reshape(-1))
+        del rho, u
+        lat.step(10)
+        ms = time_step_kernel(torch, lat, 60)
+        b = 19 * 2 * olb.STATE_ELEM[olb.DTYPES[dtype]]
+        out[f"tgv512_{dtype}_pull"] = {
+            "MLUPS": round(n ** 3 / ms / 1e3, 1), "bytes_per_update": b,
+            "roofline_frac": round(n ** 3 * b / (ms * 1e-3) / 1e9 / peak, 4)}
+        lat.close()
+        torch.cuda.empty_cache()
+    # adjoint, porous channel 256x128x128 (reduced to 200 steps, K = 100)
+    nx, ny, nz = 256, 128, 128
+    m = I.channel(nx, ny, nz)
+    lat = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype="f32", scheme="pull")
+    lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 1)
+    lat.set_bgk(0.8)
+    lat.set_force((I.channel_force(ny, 0.8), 0, 0))
+    lat.set_porosity(torch.from_numpy(I.smoothed_porosity(2, m).reshape(-1)).cuda())
+    lat.init_equilibrium()
+    steps = 200
+    lat.adjoint_run(20, 10, (0, nx - 1, 0))
+    torch.cuda.synchronize()
+    lat.init_equilibrium()
+    t = time.perf_counter()
+    lat.adjoint_run(steps, 100, (0, nx - 1, 0))
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t
+    fl = int((m == I.FLUID).sum())
+    mlups = fl * steps / sec / 1e6
+    out["adjoint_channel256_f32"] = {
+        "MLUPS": round(mlups, 1), "bytes_per_cell_step": 553,
+        "roofline_frac": round(mlups * 1e6 * 553 / 1e9 / peak, 4),
+        "note": "forward + recompute + adjoint per cell-step, 200 steps, K=100"}
+    lat.close()
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2307_11752_gb300 import build, olb
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    build.build()
+    olb.load()
+    scheme = "pull"
+    lat, m, noise = make_cavity(olb, torch, "f32", scheme)
+    fluid = int((m == I.FLUID).sum())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ms, launches, stats = time_device(torch, lat, noise, args.steps, args.warmup)
+    clocks = clk.summary()
+    kernel_ms = time_step_kernel(torch, lat, 500)
+    lat.close()
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    units = fluid * LBM_STEPS * args.steps * world
+    value = units / (ms_max * 1e-3) / 1e6
+    peak, peak_kind = measured_peak_gbs()
+    bytes_per_launch = fluid * 152
+    achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
+    traffic = profiled_traffic("d3q19_f32_pull", fluid)
+    e2e_sec, h2d, d2h = e2e_run(olb, torch, m, max(1, min(args.steps, 3)))
+    e2e_units = fluid * LBM_STEPS * max(1, min(args.steps, 3))
+    extra = variants(olb, torch) if (args.variants and rank == 0) else None
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        return
+    cfg = workload_config()
+    cfg["scheme"] = scheme
+    cfg["parallelism"] = f"replicas{world}" if world > 1 else "single-gpu"
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": cfg,
+        "roofline": {"bound": "hbm", "kernel": "k_step<D3Q19,float,pull>", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": None if traffic is None else round(traffic),
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": round(kernel_ms, 5)},
+        "e2e": {"value": round(e2e_units / e2e_sec / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "statistics_last_step": {"mass": stats[0], "max_u": stats[5], "nonfinite": stats[6]},
+    }
+    if extra is not None:
+        line["variants"] = extra
+    if args.cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------------------
+def _oracle_cavity():
+    from oracle import oracle as orc
+
+    orc.build()
+    m = I.cavity(N_SIDE)
+    wu = np.zeros((256, 3))
+    wu[I.LID] = (LID, 0.0, 0.0)
+    lat = orc.Lattice(orc.D3Q19, m, TAU, periodic=0, wall_u=wu)
+    f = lat.init_equilibrium(*I.rest(m.shape)) + I.population_noise(SEED, 19, m, 1e-6)
+    return lat, np.ascontiguousarray(f), int((m == I.FLUID).sum())
+
+
+def _threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else len(os.sched_getaffinity(0))
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload: as many LBM steps of the 128^3 cavity as fit in ~`seconds`."""
+    lat, f, fluid = _oracle_cavity()
+    t = time.perf_counter()
+    lat.step(f, 1)
+    one = time.perf_counter() - t
+    n = max(1, min(LBM_STEPS, int(seconds / max(one, 1e-6))))
+    t = time.perf_counter()
+    lat.step(f, n)
+    sec = time.perf_counter() - t
+    return {"value": round(fluid * n / sec / 1e6, 3), "unit": "MLUPS", "cores": _threads(),
+            "kind": "oracle",
+            "sample": f"{n} of the {LBM_STEPS} FP64 steps of the {N_SIDE}^3 cavity (after 1 warm-up step)"}
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    lat, f, fluid = _oracle_cavity()
+    sample = 2
+    for _ in range(args.warmup):
+        lat.step(f, 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        lat.step(f, sample)
+    sec = time.perf_counter() - t
+    value = fluid * sample * args.steps / sec / 1e6
+    cfg = workload_config()
+    cfg["storage"] = "f64"
+    cfg["parallelism"] = "cpu"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec * 1e3 / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": _threads(),
+                             "kind": "oracle",
+                             "sample": f"each step = {sample} of the {LBM_STEPS} LBM steps of the "
+                                       f"{N_SIDE}^3 cavity in the FP64 CPU oracle"},
+            "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * olb.h -- C ABI of the GB300 lattice Boltzmann library (libolb.so).
+ *
+ * The library advances the lattice Boltzmann BGK map of the OpenLB user guide
+ * (release 1.6, arXiv 2307.11752) on one NVIDIA GPU:
+ *   collision  f*_i = f_i - (f_i - f^eq_i)/tau          (section "Lattice Boltzmann Methods",
+ *                                                        collision and BGK equations; BGK listing)
+ *   streaming  f_i(t+1, x + c_i) = f*_i(t, x)           (streaming equation, same section)
+ * on the D2Q9 lattice of the "Descriptor" listing and on D3Q19 (velocities and
+ * ordering: rest, then (-1,0,0),(0,-1,0),(0,0,-1),(-1,-1,0),(-1,1,0),(-1,0,-1),
+ * (-1,0,1),(0,-1,-1),(0,-1,1), then index i+9 = -c_i), with periodic axes,
+ * halfway bounce-back walls and moving walls (BounceBack / BounceBackVelocity,
+ * section "Define Boundary Values"), a uniform Guo body force (Eqs. FBD, dF) and
+ * a per-cell porosity that scales the equilibrium velocity (section "Porous
+ * Media Model").  olb_adjoint_run returns the gradient of a plane-averaged
+ * velocity with respect to the porosity field and tau (the adjoint approach of
+ * section "Derivative Computation", taken here as the exact discrete adjoint).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Cells are numbered x fastest: cell = x + nx*(y + ny*z).  Population arrays
+ *    are structure-of-arrays [q][cells] in the canonical, unshifted form:
+ *    pre-collision populations f(t) in double precision.  Velocity arrays are
+ *    [3][cells] (the z component is 0 on D2Q9).
+ *  - Array arguments may point to device memory or to host memory (pinned or
+ *    pageable); the library asks the driver which one it is and stages host data
+ *    through a device buffer.  The caller owns every array; the library only reads
+ *    or writes it during the call (no pointer is kept).
+ *  - Work is queued on the handle's CUDA stream (olb_set_stream; default: the
+ *    legacy default stream).  Calls that return data through host pointers
+ *    synchronise that stream before returning; the others are asynchronous.
+ *  - Every call returns an olb_status.  On failure nothing observable has changed
+ *    in the handle and olb_last_error() describes the cause (thread-local string,
+ *    valid until the next call on the same thread).
+ *  - A handle is not thread-safe: one thread at a time per handle.
+ */
+#ifndef OLB_H
+#define OLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct olb_lattice* olb_handle;
+
+typedef enum { OLB_D2Q9 = 0, OLB_D3Q19 = 1 } olb_descriptor;
+
+/* Storage type of the populations on the GPU.  F64 and F32 store f_i - w_i and
+ * compute in the same precision; the *_SHIFTED types store f_i - w_i in 16 bits
+ * (round to nearest even) and compute in FP32. */
+typedef enum {
+  OLB_F64 = 0,
+  OLB_F32 = 1,
+  OLB_F16_SHIFTED = 2,
+  OLB_BF16_SHIFTED = 3
+} olb_dtype;
+
+/* Propagation pattern: PULL keeps two population buffers and gathers each cell's
+ * populations from its neighbours; AA keeps one buffer and alternates an
+ * in-place local step with an in-place neighbour step.  Both compute the same map. */
+typedef enum { OLB_PULL = 0, OLB_AA = 1 } olb_scheme;
+
+typedef enum {
+  OLB_OK = 0,
+  OLB_ERR_ARG = -1,         /* invalid argument (null handle, bad size, tau <= 1/2, ...) */
+  OLB_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+  OLB_ERR_OOM = -3,         /* the allocator returned no memory */
+  OLB_ERR_STATE = -4,       /* call not valid in the handle's current state */
+  OLB_ERR_NONFINITE = -5,   /* a NaN or Inf population was found */
+  OLB_ERR_TIMEOUT = -6,     /* reserved: no call of this version waits on the device */
+  OLB_ERR_UNSUPPORTED = -7  /* combination not implemented */
+} olb_status;
+
+/* Material numbers (section "Setting Material Numbers"). */
+enum {
+  OLB_MAT_VOID = 0,        /* outside the domain: acts as a no-slip wall, never updated */
+  OLB_MAT_FLUID = 1,       /* collided and streamed */
+  OLB_MAT_BOUNCE_BACK = 2  /* halfway no-slip wall */
+  /* 3..255: moving walls, velocity set with olb_set_wall_velocity (default 0) */
+};
+
+/* Periodicity mask bits for olb_set_material. */
+enum { OLB_PERIODIC_X = 1, OLB_PERIODIC_Y = 2, OLB_PERIODIC_Z = 4 };
+
+/* Device-memory provider for every buffer a handle owns.  alloc(size, ctx) returns
+ * device memory (at least 256-byte aligned) or NULL; free_(ptr, ctx) releases it.
+ * Passing alloc == NULL restores cudaMalloc/cudaFree.  Process-wide; affects
+ * buffers allocated after the call (each buffer is freed by the provider that
+ * allocated it).  Returns OLB_OK. */
+int olb_set_allocator(void* (*alloc)(size_t size, void* ctx),
+                      void (*free_)(void* ptr, void* ctx), void* ctx);
+
+/* Create a lattice of nx*ny*nz cells (nz must be 1 for D2Q9) on the current CUDA
+ * device.  All cells start as fluid, no axis periodic, tau = 1, no force, no
+ * porosity, populations at rest (f = w), scheme PULL, time 0.
+ * Errors: OLB_ERR_ARG (sizes < 1, more than 2^31 - 1 cells, bad enum),
+ *         OLB_ERR_OOM, OLB_ERR_CUDA. */
+int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, olb_handle* out);
+
+/* Release every buffer of the handle (after synchronising its stream). */
+int olb_lattice_destroy(olb_handle h);
+
+/* Stream for all later work of the handle (a cudaStream_t; NULL = legacy default). */
+int olb_set_stream(olb_handle h, void* cuda_stream);
+
+/* Switch the propagation pattern; the state is preserved. */
+int olb_set_scheme(olb_handle h, olb_scheme s);
+
+/* Material number of every cell (uint8 [cells]) and the periodic axes.  A link
+ * from a fluid cell to a non-fluid cell, or out of the domain along a
+ * non-periodic axis, is a halfway bounce-back link.  Populations of non-fluid
+ * cells are undefined afterwards.  Errors: OLB_ERR_ARG (null array, mask > 7,
+ * z periodic on D2Q9). */
+int olb_set_material(olb_handle h, const uint8_t* material, unsigned periodic_mask);
+
+/* Velocity u_w of moving-wall material `material_id` (3..255).  A population
+ * reflected from such a wall gains 6 w_i rho_x (c_i . u_w), rho_x the density of
+ * the fluid cell before collision (BounceBackVelocity). */
+int olb_set_wall_velocity(olb_handle h, int material_id, const double u[3]);
+
+/* BGK relaxation time (omega = 1/tau).  Errors: OLB_ERR_ARG unless tau > 1/2. */
+int olb_set_bgk(olb_handle h, double tau);
+
+/* Uniform body force density F (Guo forcing with u = (j + F/2)/rho, Eqs. FBD, dF). */
+int olb_set_force(olb_handle h, const double F[3]);
+
+/* Per-cell porosity gamma in [0,1] (double [cells]); the equilibrium and the
+ * forcing term use gamma*u (section "Porous Media Model").  The values are
+ * copied (stored in the compute precision).  NULL removes the field (gamma = 1).
+ * Errors: OLB_ERR_ARG for values outside [0,1] or non-finite. */
+int olb_set_porosity(olb_handle h, const double* gamma);
+
+/* f = f^eq(rho, u) on every cell (section "Define Initial Conditions",
+ * iniEquilibrium); rho: double [cells] or NULL (= 1); u: double [3][cells] or
+ * NULL (= 0).  Resets the time counter to 0. */
+int olb_init_equilibrium(olb_handle h, const double* rho, const double* u);
+
+/* f += df on every fluid cell (df: double [q][cells]), e.g. a seeded perturbation. */
+int olb_perturb_populations(olb_handle h, const double* df);
+
+/* Replace / read the canonical state f(t) (double [q][cells], unshifted).
+ * olb_get_populations writes non-fluid cells as 0. */
+int olb_set_populations(olb_handle h, const double* f);
+int olb_get_populations(olb_handle h, double* f);
+
+/* Advance the state by n >= 0 collide-and-stream steps (asynchronous). */
+int olb_step(olb_handle h, int64_t n);
+
+/* Advance by n >= 1 steps like olb_step and return the lattice statistics that
+ * the last step's collision evaluated (the state it collided, f(t + n - 1)), in
+ * the layout of olb_diagnostics -- OpenLB's getStatistics() after a
+ * collideAndStream ("evaluated during the previous collision step").  The
+ * statistics are accumulated inside the fused step kernel; no extra pass over
+ * the populations.  Synchronises the stream.  Returns OLB_ERR_NONFINITE (after
+ * filling out) when a non-finite population was collided. */
+int olb_step_stats(olb_handle h, int64_t n, double* out);
+
+/* Density rho (double [cells]) and velocity u = (j + F/2)/rho (double [3][cells])
+ * of the current state; non-fluid cells get 0.  Either pointer may be NULL. */
+int olb_moments(olb_handle h, double* rho, double* u);
+
+/* Lattice statistics of the current state over fluid cells (lesson "Extract
+ * Data From a Simulation"), accumulated in double precision:
+ *   out[0] sum rho, out[1..3] sum j (j = sum_i c_i f_i), out[4] sum |u|^2/2,
+ *   out[5] max |u|, out[6] number of cells holding a NaN or Inf population
+ * (such cells are left out of out[0..5]).  out is a host or device double[7];
+ * returns OLB_ERR_NONFINITE (after filling out) when out[6] > 0. */
+int olb_diagnostics(olb_handle h, double* out);
+
+/* Objective of olb_adjoint_run: mean of u[component] over the fluid cells whose
+ * coordinate along plane_axis (0 x, 1 y, 2 z) equals plane_index -- the discrete
+ * plane reduction of the flux functors (section "Discrete Flux Functor"). */
+typedef struct {
+  int32_t plane_axis;
+  int32_t plane_index;
+  int32_t component;
+} olb_objective;
+
+/* Run n_steps steps from the current state, evaluate the objective L on the final
+ * state, and return dL/dgamma (double [cells], 0 on non-fluid cells) and dL/dtau.
+ * Forward states are checkpointed every `checkpoint_every` steps and each segment
+ * is recomputed in reverse before its adjoint steps.  The handle ends in the final
+ * forward state (time advanced by n_steps), as after olb_step(h, n_steps).
+ * The gradient is with respect to the porosity field set by olb_set_porosity
+ * (gamma = 1 everywhere when none is set).  Any of loss, dL_dgamma, dL_dtau may
+ * be NULL.  Device memory: (ceil(n/K) + K) copies of the state plus two adjoint
+ * fields (K = checkpoint_every).
+ * Errors: OLB_ERR_ARG (n_steps < 1, K < 1, bad objective or empty plane),
+ *         OLB_ERR_OOM. */
+int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
+                    const olb_objective* obj, double* loss, double* dL_dgamma,
+                    double* dL_dtau);
+
+/* Block the host until all work queued on the handle's stream has finished;
+ * reports asynchronous CUDA errors as OLB_ERR_CUDA. */
+int olb_synchronize(olb_handle h);
+
+/* Time step counter (steps since the last olb_init_equilibrium /
+ * olb_set_populations) and the number of kernels the handle has launched. */
+int olb_counters(olb_handle h, int64_t* time, int64_t* kernel_launches);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char* olb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OLB_H */

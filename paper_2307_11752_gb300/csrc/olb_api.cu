@@ -1,0 +1,804 @@
+// olb_api.cu -- the C ABI of include/olb.h: handle state, argument checks,
+// host/device staging, representation bookkeeping and the checkpointed adjoint.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "olb.h"
+#include "olb_internal.h"
+#include "olb_kernels.cuh"
+
+using namespace olb;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(OLB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define OLB_CUDA(call, what)                      \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+struct Provider {
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*free_)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_provider_mu;
+Provider g_provider;
+
+// A device buffer owned by the library, released by the provider that made it.
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  Provider prov;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), prov(o.prov) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (!p) return;
+    if (prov.alloc) {
+      prov.free_(p, prov.ctx);
+    } else {
+      cudaFree(p);
+    }
+    p = nullptr;
+    n = 0;
+  }
+  // Allocate `bytes` (no-op when already at least that large).  Returns OLB status.
+  int reserve(size_t bytes) {
+    if (p && n >= bytes) return OLB_OK;
+    release();
+    if (bytes == 0) bytes = 256;
+    {
+      std::lock_guard<std::mutex> lk(g_provider_mu);
+      prov = g_provider;
+    }
+    if (prov.alloc) {
+      p = prov.alloc(bytes, prov.ctx);
+      if (!p) return fail(OLB_ERR_OOM, "allocator returned no memory for %zu bytes", bytes);
+    } else {
+      cudaError_t e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(OLB_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+      }
+    }
+    n = bytes;
+    return OLB_OK;
+  }
+};
+
+const KernelTable* table_for(int d, int t) {
+  static const KernelTable* (*tables[2][4])() = {
+      {table_d2q9_f64, table_d2q9_f32, table_d2q9_f16, table_d2q9_bf16},
+      {table_d3q19_f64, table_d3q19_f32, table_d3q19_f16, table_d3q19_bf16}};
+  if (d < 0 || d > 1 || t < 0 || t > 3) return nullptr;
+  return tables[d][t]();
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Lattice tables for host-side geometry processing (same tables as the kernels).
+template <class L>
+void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, uint8_t* cls,
+                uint32_t* wmask, bool* moving, bool* any_wall) {
+  *moving = false;
+  *any_wall = false;
+  const int e[3] = {nx, ny, nz};
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int64_t c = ((int64_t)z * ny + y) * nx + x;
+        wmask[c] = 0;
+        if (mat[c] != OLB_MAT_FLUID) {
+          cls[c] = 0;
+          *any_wall = true;
+          continue;
+        }
+        uint32_t m = 0;
+        for (int i = 1; i < L::Q; ++i) {
+          int q[3] = {x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2)};
+          bool inside = true;
+          for (int a = 0; a < 3; ++a) {
+            if (q[a] < 0 || q[a] >= e[a]) {
+              if (periodic & (1u << a)) {
+                q[a] = (q[a] + e[a]) % e[a];
+              } else {
+                inside = false;
+              }
+            }
+          }
+          if (!inside) {
+            m |= 1u << i;
+            continue;
+          }
+          const uint8_t sm = mat[((int64_t)q[2] * ny + q[1]) * nx + q[0]];
+          if (sm != OLB_MAT_FLUID) {
+            m |= 1u << i;
+            if (sm >= 3) *moving = true;
+          }
+        }
+        wmask[c] = m;
+        cls[c] = m ? 2 : 1;
+        if (m) *any_wall = true;
+      }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------------
+struct olb_lattice {
+  int desc = 0, dtype = 0, q = 0, dim = 0;
+  int nx = 0, ny = 0, nz = 0, ncell = 0;
+  const KernelTable* kt = nullptr;
+  cudaStream_t stream = nullptr;
+  DevBuf buf[2];
+  int cur = 0, repr = PRE, scheme = OLB_PULL;
+  DevBuf mat, cls, wmask, wall_u, gamma, partials, out8;
+  std::vector<uint8_t> h_mat;
+  unsigned periodic = 0;
+  bool all_fluid = false, moving = false;
+  double h_wall[256][4];
+  double tau = 1.0, F[3] = {0.0, 0.0, 0.0};
+  bool has_gamma = false;
+  int64_t time = 0, launches = 0;
+
+  size_t state_bytes() const { return (size_t)q * ncell * kt->state_elem; }
+  size_t compute_elem() const { return dtype == OLB_F64 ? sizeof(double) : sizeof(float); }
+
+  HostParams params() const {
+    HostParams p;
+    p.nx = nx;
+    p.ny = ny;
+    p.nz = nz;
+    p.ncell = ncell;
+    p.periodic = periodic;
+    p.cls = all_fluid ? nullptr : static_cast<const uint8_t*>(cls.p);
+    p.wmask = static_cast<const uint32_t*>(wmask.p);
+    p.mat = static_cast<const uint8_t*>(mat.p);
+    p.wall_u = static_cast<const double*>(wall_u.p);
+    p.moving = moving ? 1 : 0;
+    p.omega = 1.0 / tau;
+    for (int a = 0; a < 3; ++a) p.force[a] = F[a];
+    p.forced = (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0) ? 1 : 0;
+    p.gamma = has_gamma ? gamma.p : nullptr;
+    p.stream = stream;
+    return p;
+  }
+  int64_t grid_blocks() const { return make_grid(nx, ny, nz).blocks(); }
+};
+
+namespace olb {
+
+Grid make_grid(int nx, int ny, int nz) {
+  Grid g;
+  int bx = nx >= 256 ? 256 : ((nx + 31) / 32) * 32;
+  int by = 256 / bx;
+  if (by > ny) by = ny;
+  if (by < 1) by = 1;
+  g.block = dim3(bx, by, 1);
+  g.grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by, nz);
+  return g;
+}
+
+__global__ void k_reduce_rows(const double* __restrict__ rows, int64_t n, double* out) {
+  __shared__ double sh[256][8];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double v = rows[8 * r + k];
+      acc[k] = (k == 5) ? fmax(acc[k], v) : acc[k] + v;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const double o = sh[threadIdx.x + s][k];
+        sh[threadIdx.x][k] = (k == 5) ? fmax(sh[threadIdx.x][k], o) : sh[threadIdx.x][k] + o;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) out[threadIdx.x] = sh[0][threadIdx.x];
+}
+
+cudaError_t reduce_partials(const double* partials, int64_t rows, double* out, cudaStream_t s) {
+  k_reduce_rows<<<1, 256, 0, s>>>(partials, rows, out);
+  return cudaGetLastError();
+}
+
+}  // namespace olb
+
+namespace {
+
+int check(olb_handle h) {
+  if (!h) return fail(OLB_ERR_ARG, "null handle");
+  g_err.clear();
+  return OLB_OK;
+}
+
+int launched(olb_handle h, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  h->launches++;
+  return OLB_OK;
+}
+
+// Device view of a caller array of `bytes` bytes for reading.  Host memory is
+// copied into h->stage (or `tmp`) on the handle's stream.
+int input_view(olb_handle h, const void* p, size_t bytes, DevBuf& tmp, const void** out) {
+  if (is_device_pointer(p)) {
+    *out = p;
+    return OLB_OK;
+  }
+  int rc = tmp.reserve(bytes);
+  if (rc) return rc;
+  OLB_CUDA(cudaMemcpyAsync(tmp.p, p, bytes, cudaMemcpyHostToDevice, h->stream), "staging copy");
+  *out = tmp.p;
+  return OLB_OK;
+}
+
+// Ensure the second population buffer exists.
+int ensure_other(olb_handle h) {
+  DevBuf& b = h->buf[1 - h->cur];
+  if (b.p && b.n >= h->state_bytes()) return OLB_OK;
+  int rc = b.reserve(h->state_bytes());
+  if (rc) return rc;
+  OLB_CUDA(cudaMemsetAsync(b.p, 0, h->state_bytes(), h->stream), "clear buffer");
+  return OLB_OK;
+}
+
+int ensure_partials(olb_handle h, int64_t rows) {
+  int rc = h->partials.reserve((size_t)rows * 8 * sizeof(double));
+  if (rc) return rc;
+  return h->out8.reserve(8 * sizeof(double));
+}
+
+// Bring the state into the canonical PRE representation.
+int materialize(olb_handle h) {
+  if (h->repr == PRE) return OLB_OK;
+  int rc = ensure_other(h);
+  if (rc) return rc;
+  HostParams p = h->params();
+  rc = launched(h, h->kt->materialize(p, gather_of(h->repr), h->buf[h->cur].p, h->buf[1 - h->cur].p),
+                "materialize");
+  if (rc) return rc;
+  h->cur = 1 - h->cur;
+  h->repr = PRE;
+  return OLB_OK;
+}
+
+// One collide-and-stream step in the handle's scheme.
+int step_once(olb_handle h, bool stats, double* partials) {
+  HostParams p = h->params();
+  const KernelTable* kt = h->kt;
+  int rc;
+  void* a = h->buf[h->cur].p;
+  if (h->scheme == OLB_PULL) {
+    if (h->repr == PRE) {
+      rc = launched(h, kt->step(p, G_OWN, S_OWN, stats, a, a, partials), "step");
+    } else {
+      if ((rc = ensure_other(h))) return rc;
+      void* b = h->buf[1 - h->cur].p;
+      rc = launched(h, kt->step(p, gather_of(h->repr), S_OWN, stats, a, b, partials), "step");
+      if (!rc) h->cur = 1 - h->cur;
+    }
+    if (rc) return rc;
+    h->repr = POST;
+  } else {
+    if (h->repr == PRE) {
+      rc = launched(h, kt->step(p, G_OWN, S_OWN_SWAP, stats, a, a, partials), "step");
+      if (rc) return rc;
+      h->repr = AA_ODD;
+    } else if (h->repr == AA_ODD) {
+      rc = launched(h, kt->step(p, G_PULL_SWAP, S_PUSH, stats, a, a, partials), "step");
+      if (rc) return rc;
+      h->repr = PRE;
+    } else {
+      if ((rc = ensure_other(h))) return rc;
+      void* b = h->buf[1 - h->cur].p;
+      rc = launched(h, kt->step(p, G_PULL, S_OWN_SWAP, stats, a, b, partials), "step");
+      if (rc) return rc;
+      h->cur = 1 - h->cur;
+      h->repr = AA_ODD;
+    }
+  }
+  h->time++;
+  return OLB_OK;
+}
+
+// Convert the 8 reduced statistics to the ABI's 7 and deliver them.
+int deliver_stats(olb_handle h, double* out) {
+  double r[8];
+  OLB_CUDA(cudaMemcpyAsync(r, h->out8.p, sizeof(r), cudaMemcpyDeviceToHost, h->stream), "stats copy");
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "stats sync");
+  double o[7] = {r[7] + r[0], r[1], r[2], r[3], r[4], r[5], r[6]};
+  if (is_device_pointer(out)) {
+    OLB_CUDA(cudaMemcpyAsync(out, o, sizeof(o), cudaMemcpyHostToDevice, h->stream), "stats out");
+    OLB_CUDA(cudaStreamSynchronize(h->stream), "stats sync");
+  } else {
+    std::memcpy(out, o, sizeof(o));
+  }
+  if (o[6] > 0) return fail(OLB_ERR_NONFINITE, "%.0f cells hold non-finite populations", o[6]);
+  return OLB_OK;
+}
+
+int upload_wall(olb_handle h) {
+  OLB_CUDA(cudaMemcpyAsync(h->wall_u.p, h->h_wall, sizeof(h->h_wall), cudaMemcpyHostToDevice,
+                           h->stream),
+           "wall velocity upload");
+  return OLB_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------
+extern "C" {
+
+const char* olb_last_error(void) { return g_err.c_str(); }
+
+int olb_set_allocator(void* (*alloc)(size_t, void*), void (*free_)(void*, void*), void* ctx) {
+  std::lock_guard<std::mutex> lk(g_provider_mu);
+  if (alloc && !free_) return fail(OLB_ERR_ARG, "allocator without a free function");
+  g_provider.alloc = alloc;
+  g_provider.free_ = alloc ? free_ : nullptr;
+  g_provider.ctx = alloc ? ctx : nullptr;
+  g_err.clear();
+  return OLB_OK;
+}
+
+int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, olb_handle* out) {
+  g_err.clear();
+  if (!out) return fail(OLB_ERR_ARG, "null output handle pointer");
+  *out = nullptr;
+  const KernelTable* kt = table_for((int)d, (int)t);
+  if (!kt) return fail(OLB_ERR_ARG, "unknown descriptor %d or dtype %d", (int)d, (int)t);
+  if (nx < 1 || ny < 1 || nz < 1) return fail(OLB_ERR_ARG, "lattice sizes must be >= 1");
+  if (d == OLB_D2Q9 && nz != 1) return fail(OLB_ERR_ARG, "D2Q9 requires nz == 1");
+  const int64_t cells = (int64_t)nx * ny * nz;
+  if (cells > 2147483647LL) return fail(OLB_ERR_ARG, "more than 2^31 - 1 cells");
+  if (nz > 65535) return fail(OLB_ERR_ARG, "nz > 65535");
+  olb_lattice* h = new olb_lattice();
+  h->desc = (int)d;
+  h->dtype = (int)t;
+  h->kt = kt;
+  h->q = kt->q;
+  h->dim = d == OLB_D2Q9 ? 2 : 3;
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->ncell = (int)cells;
+  std::memset(h->h_wall, 0, sizeof(h->h_wall));
+  int rc;
+  if ((rc = h->buf[0].reserve(h->state_bytes())) || (rc = h->mat.reserve(cells)) ||
+      (rc = h->cls.reserve(cells)) || (rc = h->wmask.reserve(cells * 4)) ||
+      (rc = h->wall_u.reserve(sizeof(h->h_wall))) ||
+      (rc = ensure_partials(h, h->grid_blocks()))) {
+    std::string msg = g_err;
+    delete h;
+    g_err = msg;
+    return rc;
+  }
+  // all fluid, nothing periodic: every boundary link bounces back
+  h->h_mat.assign(cells, OLB_MAT_FLUID);
+  if ((rc = olb_set_material(h, h->h_mat.data(), 0)) || (rc = olb_init_equilibrium(h, nullptr, nullptr)) ||
+      (rc = olb_synchronize(h))) {
+    std::string msg = g_err;
+    delete h;
+    g_err = msg;
+    return rc;
+  }
+  *out = h;
+  return OLB_OK;
+}
+
+int olb_lattice_destroy(olb_handle h) {
+  if (!h) return fail(OLB_ERR_ARG, "null handle");
+  cudaStreamSynchronize(h->stream);
+  delete h;
+  g_err.clear();
+  return OLB_OK;
+}
+
+int olb_set_stream(olb_handle h, void* cuda_stream) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (h->stream != (cudaStream_t)cuda_stream) {
+    // order the new stream after everything queued on the old one
+    OLB_CUDA(cudaStreamSynchronize(h->stream), "stream switch");
+  }
+  h->stream = (cudaStream_t)cuda_stream;
+  return OLB_OK;
+}
+
+int olb_set_scheme(olb_handle h, olb_scheme s) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (s != OLB_PULL && s != OLB_AA) return fail(OLB_ERR_ARG, "unknown scheme %d", (int)s);
+  h->scheme = (int)s;
+  return OLB_OK;
+}
+
+int olb_set_material(olb_handle h, const uint8_t* material, unsigned periodic_mask) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!material) return fail(OLB_ERR_ARG, "null material array");
+  if (periodic_mask > 7) return fail(OLB_ERR_ARG, "periodic mask %u > 7", periodic_mask);
+  if (h->dim == 2 && (periodic_mask & OLB_PERIODIC_Z))
+    return fail(OLB_ERR_ARG, "z cannot be periodic on D2Q9");
+  const size_t n = (size_t)h->ncell;
+  std::vector<uint8_t> m(n);
+  if (is_device_pointer(material)) {
+    OLB_CUDA(cudaMemcpy(m.data(), material, n, cudaMemcpyDeviceToHost), "material read");
+  } else {
+    std::memcpy(m.data(), material, n);
+  }
+  // the current state is kept in the canonical form across the geometry change
+  if ((rc = materialize(h))) return rc;
+  std::vector<uint8_t> cls(n);
+  std::vector<uint32_t> wm(n);
+  bool moving = false, any_wall = false;
+  if (h->desc == OLB_D2Q9)
+    link_masks<D2Q9>(h->nx, h->ny, h->nz, periodic_mask, m.data(), cls.data(), wm.data(), &moving, &any_wall);
+  else
+    link_masks<D3Q19>(h->nx, h->ny, h->nz, periodic_mask, m.data(), cls.data(), wm.data(), &moving, &any_wall);
+  OLB_CUDA(cudaMemcpyAsync(h->mat.p, m.data(), n, cudaMemcpyHostToDevice, h->stream), "material upload");
+  OLB_CUDA(cudaMemcpyAsync(h->cls.p, cls.data(), n, cudaMemcpyHostToDevice, h->stream), "class upload");
+  OLB_CUDA(cudaMemcpyAsync(h->wmask.p, wm.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "mask upload");
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "material sync");
+  h->h_mat.swap(m);
+  h->periodic = periodic_mask;
+  h->moving = moving;
+  h->all_fluid = !any_wall;
+  return upload_wall(h);
+}
+
+int olb_set_wall_velocity(olb_handle h, int material_id, const double u[3]) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (material_id < 3 || material_id > 255) return fail(OLB_ERR_ARG, "material %d is not a moving wall id", material_id);
+  if (!u) return fail(OLB_ERR_ARG, "null velocity");
+  for (int a = 0; a < 3; ++a) {
+    if (!std::isfinite(u[a])) return fail(OLB_ERR_ARG, "non-finite wall velocity");
+  }
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "wall sync");
+  for (int a = 0; a < 3; ++a) h->h_wall[material_id][a] = (h->dim == 2 && a == 2) ? 0.0 : u[a];
+  return upload_wall(h);
+}
+
+int olb_set_bgk(olb_handle h, double tau) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(OLB_ERR_ARG, "tau must be > 1/2 (got %g)", tau);
+  h->tau = tau;
+  return OLB_OK;
+}
+
+int olb_set_force(olb_handle h, const double F[3]) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!F) return fail(OLB_ERR_ARG, "null force");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(F[a])) return fail(OLB_ERR_ARG, "non-finite force");
+  for (int a = 0; a < 3; ++a) h->F[a] = (h->dim == 2 && a == 2) ? 0.0 : F[a];
+  return OLB_OK;
+}
+
+}  // extern "C"
+
+namespace olb {
+template <class C>
+__global__ void k_convert_gamma(const double* __restrict__ in, C* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (C)in[i];
+}
+}  // namespace olb
+
+extern "C" {
+
+int olb_set_porosity(olb_handle h, const double* gamma) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!gamma) {
+    h->has_gamma = false;
+    return OLB_OK;
+  }
+  DevBuf tmp;
+  const void* g;
+  if ((rc = input_view(h, gamma, (size_t)h->ncell * sizeof(double), tmp, &g))) return rc;
+  if ((rc = h->gamma.reserve((size_t)h->ncell * h->compute_elem()))) return rc;
+  const int nb = (h->ncell + 255) / 256;
+  if (h->dtype == OLB_F64)
+    k_convert_gamma<double><<<nb, 256, 0, h->stream>>>(static_cast<const double*>(g), static_cast<double*>(h->gamma.p), h->ncell);
+  else
+    k_convert_gamma<float><<<nb, 256, 0, h->stream>>>(static_cast<const double*>(g), static_cast<float*>(h->gamma.p), h->ncell);
+  if ((rc = launched(h, cudaGetLastError(), "porosity"))) return rc;
+  if (tmp.p) OLB_CUDA(cudaStreamSynchronize(h->stream), "porosity sync");
+  h->has_gamma = true;
+  return OLB_OK;
+}
+
+int olb_init_equilibrium(olb_handle h, const double* rho, const double* u) {
+  int rc = check(h);
+  if (rc) return rc;
+  DevBuf t1, t2;
+  const void* r = nullptr;
+  const void* v = nullptr;
+  if (rho && (rc = input_view(h, rho, (size_t)h->ncell * sizeof(double), t1, &r))) return rc;
+  if (u && (rc = input_view(h, u, (size_t)3 * h->ncell * sizeof(double), t2, &v))) return rc;
+  HostParams p = h->params();
+  if ((rc = launched(h, h->kt->init_eq(p, static_cast<const double*>(r), static_cast<const double*>(v), h->buf[h->cur].p), "init_equilibrium")))
+    return rc;
+  if (t1.p || t2.p) OLB_CUDA(cudaStreamSynchronize(h->stream), "init sync");
+  h->repr = PRE;
+  h->time = 0;
+  return OLB_OK;
+}
+
+int olb_perturb_populations(olb_handle h, const double* df) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!df) return fail(OLB_ERR_ARG, "null perturbation");
+  DevBuf tmp;
+  const void* d;
+  if ((rc = input_view(h, df, (size_t)h->q * h->ncell * sizeof(double), tmp, &d))) return rc;
+  if ((rc = materialize(h))) return rc;
+  HostParams p = h->params();
+  if ((rc = launched(h, h->kt->perturb(p, static_cast<const double*>(d), h->buf[h->cur].p), "perturb"))) return rc;
+  if (tmp.p) OLB_CUDA(cudaStreamSynchronize(h->stream), "perturb sync");
+  return OLB_OK;
+}
+
+int olb_set_populations(olb_handle h, const double* f) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!f) return fail(OLB_ERR_ARG, "null populations");
+  DevBuf tmp;
+  const void* d;
+  if ((rc = input_view(h, f, (size_t)h->q * h->ncell * sizeof(double), tmp, &d))) return rc;
+  HostParams p = h->params();
+  if ((rc = launched(h, h->kt->from_f64(p, static_cast<const double*>(d), h->buf[h->cur].p), "set_populations"))) return rc;
+  if (tmp.p) OLB_CUDA(cudaStreamSynchronize(h->stream), "set sync");
+  h->repr = PRE;
+  h->time = 0;
+  return OLB_OK;
+}
+
+int olb_get_populations(olb_handle h, double* f) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!f) return fail(OLB_ERR_ARG, "null output");
+  const size_t bytes = (size_t)h->q * h->ncell * sizeof(double);
+  const bool dev = is_device_pointer(f);
+  DevBuf tmp;
+  if (!dev && (rc = tmp.reserve(bytes))) return rc;
+  double* d = dev ? f : static_cast<double*>(tmp.p);
+  HostParams p = h->params();
+  if ((rc = launched(h, h->kt->to_f64(p, gather_of(h->repr), h->buf[h->cur].p, d), "get_populations"))) return rc;
+  if (!dev) {
+    OLB_CUDA(cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, h->stream), "populations copy");
+    OLB_CUDA(cudaStreamSynchronize(h->stream), "populations sync");
+  }
+  return OLB_OK;
+}
+
+int olb_step(olb_handle h, int64_t n) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (n < 0) return fail(OLB_ERR_ARG, "negative step count");
+  for (int64_t s = 0; s < n; ++s)
+    if ((rc = step_once(h, false, nullptr))) return rc;
+  return OLB_OK;
+}
+
+int olb_step_stats(olb_handle h, int64_t n, double* out) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (n < 1) return fail(OLB_ERR_ARG, "olb_step_stats needs n >= 1");
+  if (!out) return fail(OLB_ERR_ARG, "null output");
+  const int64_t rows = h->grid_blocks();
+  if ((rc = ensure_partials(h, rows))) return rc;
+  for (int64_t s = 0; s + 1 < n; ++s)
+    if ((rc = step_once(h, false, nullptr))) return rc;
+  if ((rc = step_once(h, true, static_cast<double*>(h->partials.p)))) return rc;
+  if ((rc = launched(h, reduce_partials(static_cast<double*>(h->partials.p), rows, static_cast<double*>(h->out8.p), h->stream), "stats reduce")))
+    return rc;
+  return deliver_stats(h, out);
+}
+
+int olb_moments(olb_handle h, double* rho, double* u) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!rho && !u) return OLB_OK;
+  const size_t nr = (size_t)h->ncell * sizeof(double), nu = 3 * nr;
+  const bool dr = rho ? is_device_pointer(rho) : true;
+  const bool du = u ? is_device_pointer(u) : true;
+  DevBuf t1, t2;
+  if (rho && !dr && (rc = t1.reserve(nr))) return rc;
+  if (u && !du && (rc = t2.reserve(nu))) return rc;
+  double* r = rho ? (dr ? rho : static_cast<double*>(t1.p)) : nullptr;
+  double* v = u ? (du ? u : static_cast<double*>(t2.p)) : nullptr;
+  HostParams p = h->params();
+  if ((rc = launched(h, h->kt->moments(p, gather_of(h->repr), h->buf[h->cur].p, r, v), "moments"))) return rc;
+  if (rho && !dr) OLB_CUDA(cudaMemcpyAsync(rho, r, nr, cudaMemcpyDeviceToHost, h->stream), "rho copy");
+  if (u && !du) OLB_CUDA(cudaMemcpyAsync(u, v, nu, cudaMemcpyDeviceToHost, h->stream), "u copy");
+  if (!dr || !du) OLB_CUDA(cudaStreamSynchronize(h->stream), "moments sync");
+  return OLB_OK;
+}
+
+int olb_diagnostics(olb_handle h, double* out) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!out) return fail(OLB_ERR_ARG, "null output");
+  const int64_t rows = h->grid_blocks();
+  if ((rc = ensure_partials(h, rows))) return rc;
+  HostParams p = h->params();
+  if ((rc = launched(h, h->kt->stats(p, gather_of(h->repr), h->buf[h->cur].p, static_cast<double*>(h->partials.p)), "diagnostics")))
+    return rc;
+  if ((rc = launched(h, reduce_partials(static_cast<double*>(h->partials.p), rows, static_cast<double*>(h->out8.p), h->stream), "diagnostics reduce")))
+    return rc;
+  return deliver_stats(h, out);
+}
+
+int olb_synchronize(olb_handle h) {
+  int rc = check(h);
+  if (rc) return rc;
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+  OLB_CUDA(cudaGetLastError(), "asynchronous error");
+  return OLB_OK;
+}
+
+int olb_counters(olb_handle h, int64_t* time, int64_t* kernel_launches) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (time) *time = h->time;
+  if (kernel_launches) *kernel_launches = h->launches;
+  return OLB_OK;
+}
+
+int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t K, const olb_objective* obj,
+                    double* loss, double* dL_dgamma, double* dL_dtau) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (n_steps < 1 || K < 1) return fail(OLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+  if (!obj || obj->plane_axis < 0 || obj->plane_axis >= h->dim || obj->component < 0 || obj->component >= h->dim)
+    return fail(OLB_ERR_ARG, "bad objective");
+  const int ext[3] = {h->nx, h->ny, h->nz};
+  if (obj->plane_index < 0 || obj->plane_index >= ext[obj->plane_axis])
+    return fail(OLB_ERR_ARG, "objective plane index out of range");
+  int64_t count = 0;
+  for (int z = 0; z < h->nz; ++z)
+    for (int y = 0; y < h->ny; ++y)
+      for (int x = 0; x < h->nx; ++x) {
+        const int c[3] = {x, y, z};
+        if (c[obj->plane_axis] == obj->plane_index && h->h_mat[((int64_t)z * h->ny + y) * h->nx + x] == OLB_MAT_FLUID)
+          ++count;
+      }
+  if (count == 0) return fail(OLB_ERR_ARG, "objective plane holds no fluid cell");
+  if (K > n_steps) K = n_steps;
+  const int64_t nseg = (n_steps + K - 1) / K;
+  const size_t sb = h->state_bytes();
+  const size_t lb = (size_t)h->q * h->ncell * h->kt->lambda_elem;
+  const int64_t rows = h->grid_blocks();
+
+  // buffers: checkpoints, segment slots 1..K-1, two adjoint fields, gradients
+  std::vector<DevBuf> ckpt(nseg), seg(K);
+  std::vector<int> ckpt_repr(nseg);
+  DevBuf lam[2], dg, part;
+  for (auto& b : ckpt)
+    if ((rc = b.reserve(sb))) return rc;
+  for (int64_t k = 1; k < K; ++k)
+    if ((rc = seg[k].reserve(sb))) return rc;
+  if ((rc = lam[0].reserve(lb)) || (rc = lam[1].reserve(lb)) || (rc = dg.reserve((size_t)h->ncell * 8)) ||
+      (rc = part.reserve((size_t)rows * 8 * sizeof(double))) || (rc = ensure_partials(h, rows)))
+    return rc;
+  if (h->repr == AA_ODD && (rc = materialize(h))) return rc;
+
+  // forward sweep with checkpoints (pull pattern)
+  const int saved_scheme = h->scheme;
+  h->scheme = OLB_PULL;
+  for (int64_t s = 0; s < nseg; ++s) {
+    OLB_CUDA(cudaMemcpyAsync(ckpt[s].p, h->buf[h->cur].p, sb, cudaMemcpyDeviceToDevice, h->stream), "checkpoint");
+    ckpt_repr[s] = h->repr;
+    const int64_t ks = std::min<int64_t>(K, n_steps - s * K);
+    for (int64_t k = 0; k < ks; ++k)
+      if ((rc = step_once(h, false, nullptr))) {
+        h->scheme = saved_scheme;
+        return rc;
+      }
+  }
+  h->scheme = saved_scheme;
+
+  // objective and seed lam^N
+  HostParams p = h->params();
+  const KernelTable* kt = h->kt;
+  double* partials = static_cast<double*>(h->partials.p);
+  if ((rc = launched(h, kt->loss_seed(p, gather_of(h->repr), h->buf[h->cur].p, obj->plane_axis, obj->plane_index,
+                                      obj->component, 1.0 / (double)count, lam[0].p, partials), "loss")))
+    return rc;
+  if ((rc = launched(h, reduce_partials(partials, rows, static_cast<double*>(h->out8.p), h->stream), "loss reduce")))
+    return rc;
+  double lsum[8];
+  OLB_CUDA(cudaMemcpyAsync(lsum, h->out8.p, sizeof(lsum), cudaMemcpyDeviceToHost, h->stream), "loss copy");
+  OLB_CUDA(cudaMemsetAsync(dg.p, 0, (size_t)h->ncell * 8, h->stream), "gradient clear");
+  OLB_CUDA(cudaMemsetAsync(part.p, 0, (size_t)rows * 8 * sizeof(double), h->stream), "partials clear");
+
+  // reverse sweep: recompute each segment, then step the adjoint back through it
+  int li = 0;
+  for (int64_t s = nseg - 1; s >= 0; --s) {
+    const int64_t ks = std::min<int64_t>(K, n_steps - s * K);
+    std::vector<const void*> slot(ks);
+    std::vector<int> srepr(ks);
+    slot[0] = ckpt[s].p;
+    srepr[0] = ckpt_repr[s];
+    for (int64_t k = 1; k < ks; ++k) {
+      const int g = srepr[k - 1] == PRE ? G_OWN : G_PULL;
+      if ((rc = launched(h, kt->step(p, g, S_OWN, false, slot[k - 1], seg[k].p, nullptr), "recompute"))) return rc;
+      slot[k] = seg[k].p;
+      srepr[k] = POST;
+    }
+    for (int64_t k = ks - 1; k >= 0; --k) {
+      const int g = srepr[k] == PRE ? G_OWN : G_PULL;
+      if ((rc = launched(h, kt->adjoint(p, g, slot[k], lam[li].p, lam[1 - li].p, static_cast<double*>(dg.p),
+                                        static_cast<double*>(part.p)), "adjoint")))
+        return rc;
+      li = 1 - li;
+    }
+  }
+  if ((rc = launched(h, reduce_partials(static_cast<double*>(part.p), rows, static_cast<double*>(h->out8.p), h->stream), "gradient reduce")))
+    return rc;
+  double gsum[8];
+  OLB_CUDA(cudaMemcpyAsync(gsum, h->out8.p, sizeof(gsum), cudaMemcpyDeviceToHost, h->stream), "gradient copy");
+  if (dL_dgamma) {
+    OLB_CUDA(cudaMemcpyAsync(dL_dgamma, dg.p, (size_t)h->ncell * 8, cudaMemcpyDefault, h->stream), "gradient out");
+  }
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "adjoint sync");
+  if (loss) *loss = lsum[0] / (double)count;
+  if (dL_dtau) *dL_dtau = -gsum[0] / (h->tau * h->tau);
+  return OLB_OK;
+}
+
+}  // extern "C"

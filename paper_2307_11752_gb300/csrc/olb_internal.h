@@ -1,0 +1,83 @@
+// olb_internal.h -- host-side declarations shared by the ABI layer (olb_api.cu)
+// and the per-lattice, per-storage-type kernel instantiation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace olb {
+
+// State representations of a population buffer.
+//   PRE     buffer holds f(t) at the cell's own slots (canonical layout)
+//   POST    buffer holds f*(t-1) at the cell's own slots; f(t) = S f*(t-1) is
+//           obtained by pulling from the neighbours (two-buffer pull scheme)
+//   AA_ODD  buffer holds f*(t-1) with swapped slots (f*_i(x) at slot opp(i) of x),
+//           the state between the two half-steps of the AA pattern
+enum Repr { PRE = 0, POST = 1, AA_ODD = 2 };
+
+// How a kernel reads f(t) of a cell and writes the post-collision values.
+enum Gather { G_OWN = 0, G_PULL = 1, G_PULL_SWAP = 2 };
+enum Scatter { S_OWN = 0, S_OWN_SWAP = 1, S_PUSH = 2 };
+
+inline int gather_of(int repr) { return repr == PRE ? G_OWN : (repr == POST ? G_PULL : G_PULL_SWAP); }
+
+// Everything a kernel needs to know about the lattice, in double precision;
+// each instantiation unit converts it to its compute type.
+struct HostParams {
+  int nx, ny, nz;
+  int ncell;
+  unsigned periodic;
+  const uint8_t* cls;     // per cell: 0 non-fluid, 1 fluid with only fluid links, 2 fluid with wall links
+  const uint32_t* wmask;  // per cell: bit i set when the pull source x - c_i is not a fluid cell
+  const uint8_t* mat;     // material numbers
+  const double* wall_u;   // [256][4] moving-wall velocities
+  int moving;             // a moving-wall material touches the fluid
+  double omega;
+  double force[3];
+  int forced;
+  const void* gamma;      // per-cell porosity in the compute type, or nullptr
+  cudaStream_t stream;
+};
+
+// Launch geometry: 2D blocks along (x, y), one z plane per grid z index.
+struct Grid {
+  dim3 block, grid;
+  int64_t blocks() const { return (int64_t)grid.x * grid.y * grid.z; }
+};
+Grid make_grid(int nx, int ny, int nz);
+
+// Launchers of one (lattice, storage type) pair.  Each returns the CUDA error of
+// the launch.  `partials` receives one row of 8 doubles per block (reductions).
+struct KernelTable {
+  int q;
+  size_t state_elem;   // bytes per stored population
+  size_t lambda_elem;  // bytes per adjoint population
+  cudaError_t (*step)(const HostParams&, int gather, int scatter, bool stats, const void* src,
+                      void* dst, double* partials);
+  cudaError_t (*to_f64)(const HostParams&, int gather, const void* src, double* f);
+  cudaError_t (*moments)(const HostParams&, int gather, const void* src, double* rho, double* u);
+  cudaError_t (*stats)(const HostParams&, int gather, const void* src, double* partials);
+  cudaError_t (*from_f64)(const HostParams&, const double* f, void* dst);
+  cudaError_t (*init_eq)(const HostParams&, const double* rho, const double* u, void* dst);
+  cudaError_t (*perturb)(const HostParams&, const double* df, void* dst);
+  cudaError_t (*materialize)(const HostParams&, int gather, const void* src, void* dst);
+  cudaError_t (*adjoint)(const HostParams&, int gather, const void* state, const void* lam_in,
+                         void* lam_out, double* dgamma, double* partials);
+  cudaError_t (*loss_seed)(const HostParams&, int gather, const void* src, int axis, int index,
+                           int comp, double inv_count, void* lam, double* partials);
+};
+
+// dtype: 0 f64, 1 f32, 2 f16 (shifted), 3 bf16 (shifted)
+const KernelTable* table_d2q9_f64();
+const KernelTable* table_d2q9_f32();
+const KernelTable* table_d2q9_f16();
+const KernelTable* table_d2q9_bf16();
+const KernelTable* table_d3q19_f64();
+const KernelTable* table_d3q19_f32();
+const KernelTable* table_d3q19_f16();
+const KernelTable* table_d3q19_bf16();
+
+// Sum the first `rows` rows of 8 doubles into out[8] (deterministic order).
+cudaError_t reduce_partials(const double* partials, int64_t rows, double* out, cudaStream_t s);
+
+}  // namespace olb

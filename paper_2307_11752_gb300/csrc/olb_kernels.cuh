@@ -1,0 +1,894 @@
+// olb_kernels.cuh -- sm_103a kernels of the fused BGK collide-and-stream update.
+//
+// One thread updates one cell.  Populations are structure-of-arrays planes
+// [q][cells] (x fastest) holding f_i - w_i ("weight-shifted": the rest state is
+// all zero bits, and 16-bit storage spends its precision on the deviation from
+// rest).  The update is bandwidth-bound (about 200 flops against 2 x q stored
+// values per cell), so the design goal is one coalesced read and one coalesced
+// write of every population per step and nothing else on the common path:
+//   * bulk cells (all q neighbours fluid) take no branch on boundaries; periodic
+//     axes are handled by wrapped row/column indices computed once per thread;
+//   * cells next to a wall read one extra 32-bit mask with one bit per link;
+//     moving-wall velocities are looked up only on those links;
+//   * the streaming pattern is a template parameter: two-buffer pull (read the
+//     neighbours, write the own cell) or the in-place AA pattern (even step: own
+//     cell, swapped slots; odd step: read and write the neighbours' slots).
+//
+// The method (OpenLB user guide, arXiv 2307.11752):
+//   collision  f*_i = f_i + omega (f^eq_i - f_i)           BGK equation and listing
+//   forcing    + (1 - omega/2) w_i (3 (c_i - u') + 9 (c_i.u') c_i) . F,  u = (j + F/2)/rho   Eqs. FBD, dF
+//   porosity   u' = gamma u in the equilibrium and forcing terms            section "Porous Media Model"
+//   streaming  f_i(t+1, x + c_i) = f*_i(t, x)                               streaming equation
+//   bounce-back (halfway) f_opp(i)(t+1, x) = f*_i(t, x) [- 6 w_i rho_x c_i.u_w on moving walls]
+// with the second-order equilibrium
+//   f^eq_i - w_i = w_i [(rho - 1) + rho (3 c_i.u' + 4.5 (c_i.u')^2 - 1.5 u'.u')].
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "olb_internal.h"
+
+namespace olb {
+
+// ---------------------------------------------------------------------------------
+// Lattices.  D2Q9 as printed in the guide's "Descriptor" listing; D3Q19 with rest,
+// then the nine velocities whose first non-zero component is -1, then their
+// opposites (index i + 9 = -c_i).  Pairs (i, i + HALF) are opposite velocities.
+// ---------------------------------------------------------------------------------
+struct D2Q9 {
+  static constexpr int Q = 9, DIM = 2, HALF = 4;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    constexpr int t[9][3] = {{0, 0, 0},  {-1, 1, 0}, {-1, 0, 0}, {-1, -1, 0}, {0, -1, 0},
+                             {1, -1, 0}, {1, 0, 0},  {1, 1, 0},  {0, 1, 0}};
+    return t[i][a];
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : ((i % 2) == 0 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+};
+
+struct D3Q19 {
+  static constexpr int Q = 19, DIM = 3, HALF = 9;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    constexpr int t[19][3] = {{0, 0, 0},   {-1, 0, 0}, {0, -1, 0}, {0, 0, -1}, {-1, -1, 0},
+                              {-1, 1, 0},  {-1, 0, -1}, {-1, 0, 1}, {0, -1, -1}, {0, -1, 1},
+                              {1, 0, 0},   {0, 1, 0},  {0, 0, 1},  {1, 1, 0},  {1, -1, 0},
+                              {1, 0, 1},   {1, 0, -1}, {0, 1, 1},  {0, 1, -1}};
+    return t[i][a];
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (((i - 1) % 9) < 3 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+template <class L>
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : (i <= L::HALF ? i + L::HALF : i - L::HALF);
+}
+
+// ---------------------------------------------------------------------------------
+// Storage types: load/store with conversion to the compute type.
+// ---------------------------------------------------------------------------------
+template <class S>
+struct Store;
+template <>
+struct Store<double> {
+  using C = double;
+  __device__ static C ld(const double* p) { return *p; }
+  __device__ static void st(double* p, C v) { *p = v; }
+};
+template <>
+struct Store<float> {
+  using C = float;
+  __device__ static C ld(const float* p) { return *p; }
+  __device__ static void st(float* p, C v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+  using C = float;
+  __device__ static C ld(const __half* p) { return __half2float(*p); }
+  __device__ static void st(__half* p, C v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  using C = float;
+  __device__ static C ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ static void st(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Kernel parameters in the compute type C.
+template <class C>
+struct Params {
+  int nx, ny, nz, ncell;
+  unsigned periodic;
+  int all_fluid;  // every cell fluid and every axis periodic: no class reads
+  const uint8_t* __restrict__ cls;
+  const uint32_t* __restrict__ wmask;
+  const uint8_t* __restrict__ mat;
+  const double* __restrict__ wall_u;  // [256][4]
+  int moving;
+  C omega, half_force[3], force[3];
+  int forced;
+  const C* __restrict__ gamma;
+};
+
+template <class C>
+Params<C> to_params(const HostParams& h) {
+  Params<C> p;
+  p.nx = h.nx;
+  p.ny = h.ny;
+  p.nz = h.nz;
+  p.ncell = h.ncell;
+  p.periodic = h.periodic;
+  p.all_fluid = 0;
+  p.cls = h.cls;
+  p.wmask = h.wmask;
+  p.mat = h.mat;
+  p.wall_u = h.wall_u;
+  p.moving = h.moving;
+  p.omega = (C)h.omega;
+  for (int a = 0; a < 3; ++a) {
+    p.force[a] = (C)h.force[a];
+    p.half_force[a] = (C)(0.5 * h.force[a]);
+  }
+  p.forced = h.forced;
+  p.gamma = reinterpret_cast<const C*>(h.gamma);
+  return p;
+}
+
+// ---------------------------------------------------------------------------------
+// Neighbourhood of one cell: wrapped x indices and row bases for the 3 x 3
+// (dy, dz) offsets; at(dx, dy, dz) is the flat index of cell + (dx, dy, dz).
+// ---------------------------------------------------------------------------------
+struct Nbr {
+  int x, y, z, cell;
+  int xo[3];
+  int row[3][3];
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    return row[dz + 1][dy + 1] + xo[dx + 1];
+  }
+};
+
+template <class L, class C>
+__device__ __forceinline__ Nbr make_nbr(const Params<C>& p, int x, int y, int z) {
+  Nbr n;
+  n.x = x;
+  n.y = y;
+  n.z = z;
+  n.xo[0] = x == 0 ? p.nx - 1 : x - 1;
+  n.xo[1] = x;
+  n.xo[2] = x == p.nx - 1 ? 0 : x + 1;
+  const int ys[3] = {y == 0 ? p.ny - 1 : y - 1, y, y == p.ny - 1 ? 0 : y + 1};
+  int zs[3] = {z, z, z};
+  if (L::DIM == 3) {
+    zs[0] = z == 0 ? p.nz - 1 : z - 1;
+    zs[2] = z == p.nz - 1 ? 0 : z + 1;
+  }
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) n.row[dz][dy] = (zs[dz] * p.ny + ys[dy]) * p.nx;
+  n.cell = n.row[1][1] + x;
+  return n;
+}
+
+// Material number of the cell at offset (dx, dy, dz); 0 (void) outside the
+// domain along a non-periodic axis.  Only used on moving-wall links.
+template <class C>
+__device__ __forceinline__ int link_material(const Params<C>& p, const Nbr& n, int dx, int dy,
+                                             int dz) {
+  int q[3] = {n.x + dx, n.y + dy, n.z + dz};
+  const int e[3] = {p.nx, p.ny, p.nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (q[a] < 0 || q[a] >= e[a]) {
+      if (!(p.periodic & (1u << a))) return 0;
+      q[a] = q[a] < 0 ? q[a] + e[a] : q[a] - e[a];
+    }
+  }
+  return p.mat[(q[2] * p.ny + q[1]) * p.nx + q[0]];
+}
+
+// 6 w_i (c_i . u_w) of wall material m.
+template <class L, class C>
+__device__ __forceinline__ C wall_term(const Params<C>& p, int i, int m) {
+  const double* u = p.wall_u + 4 * m;
+  double cu = L::c(i, 0) * u[0] + L::c(i, 1) * u[1] + L::c(i, 2) * u[2];
+  return (C)(6.0 * L::w(i) * cu);
+}
+
+// Pull form: f_i(x) from slot i (G_PULL) or slot opp(i) (G_PULL_SWAP) of x - c_i,
+// with halfway bounce-back on wall links.
+template <class L, class S, int G>
+__device__ __forceinline__ void gather_links(const Params<typename Store<S>::C>& p, const S* src,
+                                             const Nbr& n, int cls,
+                                             typename Store<S>::C (&f)[L::Q]) {
+  using C = typename Store<S>::C;
+  const size_t N = (size_t)p.ncell;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const int slot = (G == G_PULL) ? i : opp<L>(i);
+    f[i] = Store<S>::ld(src + slot * N + n.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
+  }
+  if (cls == 2) {
+    const uint32_t m = p.wmask[n.cell];
+    C rho_x = C(0);
+    bool have_rho = false;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+      if (m & (1u << i)) {
+        // halfway bounce-back: the population that left this cell towards the wall
+        const int own = (G == G_PULL) ? opp<L>(i) : i;
+        C v = Store<S>::ld(src + own * N + n.cell);
+        if (p.moving) {
+          const int wm = link_material(p, n, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+          if (wm >= 3) {
+            if (!have_rho) {
+              rho_x = C(1);
+#pragma unroll
+              for (int j = 0; j < L::Q; ++j) rho_x += Store<S>::ld(src + j * N + n.cell);
+              have_rho = true;
+            }
+            v += rho_x * wall_term<L>(p, i, wm);
+          }
+        }
+        f[i] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Gather f(t) of one cell (shifted values, compute type) from a buffer in
+// representation G.
+// ---------------------------------------------------------------------------------
+template <class L, class S, int G>
+__device__ __forceinline__ void gather(const Params<typename Store<S>::C>& p, const S* src,
+                                       const Nbr& n, int cls,
+                                       typename Store<S>::C (&f)[L::Q]) {
+  if constexpr (G == G_OWN) {
+    const size_t N = (size_t)p.ncell;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) f[i] = Store<S>::ld(src + i * N + n.cell);
+  } else {
+    gather_links<L, S, G>(p, src, n, cls, f);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Moments and collision on shifted populations.
+// ---------------------------------------------------------------------------------
+template <class L, class C>
+__device__ __forceinline__ void moments(const C (&f)[L::Q], C& drho, C (&j)[3]) {
+  drho = f[0];
+  j[0] = j[1] = j[2] = C(0);
+#pragma unroll
+  for (int k = 1; k <= L::HALF; ++k) {
+    const int kp = k + L::HALF;  // c_kp = -c_k
+    const C s = f[k] + f[kp];
+    const C a = f[kp] - f[k];
+    drho += s;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (L::c(kp, d) == 1) j[d] += a;
+      if (L::c(kp, d) == -1) j[d] -= a;
+    }
+  }
+}
+
+// BGK collision (+ Guo forcing, + porosity) in place.  Returns rho and the
+// unscaled velocity u = (j + F/2)/rho through the out parameters.
+template <class L, class C>
+__device__ __forceinline__ void collide(const Params<C>& p, C gamma, C (&f)[L::Q], C drho,
+                                        const C (&j)[3], C& rho_out, C (&u_out)[3]) {
+  const C rho = C(1) + drho;
+  const C inv = C(1) / rho;
+  C u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) u[d] = (j[d] + p.half_force[d]) * inv;
+  rho_out = rho;
+  u_out[0] = u[0];
+  u_out[1] = u[1];
+  u_out[2] = u[2];
+  const C up[3] = {gamma * u[0], gamma * u[1], gamma * u[2]};
+  const C usq = up[0] * up[0] + up[1] * up[1] + (L::DIM == 3 ? up[2] * up[2] : C(0));
+  const C om = p.omega;
+  const C rs = C(1.5) * rho * usq;
+  const C gf = C(1) - C(0.5) * om;
+  C uF = C(0);
+  if (p.forced) uF = up[0] * p.force[0] + up[1] * p.force[1] + up[2] * p.force[2];
+  {
+    const C w0 = (C)L::w(0);
+    C feq = w0 * (drho - rs);
+    f[0] += om * (feq - f[0]);
+    if (p.forced) f[0] -= gf * w0 * C(3) * uF;
+  }
+#pragma unroll
+  for (int k = 1; k <= L::HALF; ++k) {
+    const int kp = k + L::HALF;
+    const C wk = (C)L::w(k);
+    C cu = C(0), cF = C(0);
+#pragma unroll
+    for (int d = 0; d < L::DIM; ++d) {
+      if (L::c(kp, d) == 1) {
+        cu += up[d];
+        cF += p.force[d];
+      }
+      if (L::c(kp, d) == -1) {
+        cu -= up[d];
+        cF -= p.force[d];
+      }
+    }
+    const C sym = wk * (drho + rho * (C(4.5) * cu * cu) - rs);
+    const C anti = wk * C(3) * rho * cu;
+    f[kp] += om * (sym + anti - f[kp]);
+    f[k] += om * (sym - anti - f[k]);
+    if (p.forced) {
+      const C gs = gf * wk * (C(9) * cu * cF - C(3) * uF);
+      const C ga = gf * wk * C(3) * cF;
+      f[kp] += gs + ga;
+      f[k] += gs - ga;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Scatter post-collision values to a buffer with pattern SC.
+// ---------------------------------------------------------------------------------
+template <class L, class S, int SC>
+__device__ __forceinline__ void scatter(const Params<typename Store<S>::C>& p, S* dst,
+                                        const Nbr& n, int cls,
+                                        const typename Store<S>::C (&f)[L::Q],
+                                        typename Store<S>::C rho) {
+  using C = typename Store<S>::C;
+  const size_t N = (size_t)p.ncell;
+  if (SC == S_OWN) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + i * N + n.cell, f[i]);
+  } else if (SC == S_OWN_SWAP) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + opp<L>(i) * N + n.cell, f[i]);
+  } else {  // S_PUSH: f*_i goes to slot i of x + c_i, or bounces back into slot opp(i) of x
+    if (cls == 1) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i)
+        Store<S>::st(dst + i * N + n.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), f[i]);
+    } else {
+      const uint32_t m = p.wmask[n.cell];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        if (i != 0 && (m & (1u << opp<L>(i)))) {
+          C v = f[i];
+          if (p.moving) {
+            const int wm = link_material(p, n, L::c(i, 0), L::c(i, 1), L::c(i, 2));
+            if (wm >= 3) v -= rho * wall_term<L>(p, i, wm);
+          }
+          Store<S>::st(dst + opp<L>(i) * N + n.cell, v);
+        } else {
+          Store<S>::st(dst + i * N + n.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), f[i]);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Block reduction of 8 per-thread values into one row of `partials`:
+// entries 0..4 and 6..7 are sums, entry 5 is a maximum.  Warp stage in the compute
+// type, block and global stages in double.
+// ---------------------------------------------------------------------------------
+template <class C>
+__device__ __forceinline__ void block_reduce_row(C (&v)[8], double* row, bool accumulate) {
+  __shared__ double sh[32][8];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      C other = __shfl_xor_sync(0xffffffffu, v[k], o);
+      v[k] = (k == 5) ? (other > v[k] ? other : v[k]) : v[k] + other;
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sh[warp][k] = (double)v[k];
+  }
+  __syncthreads();
+  if (tid < 8) {
+    double acc = sh[0][tid];
+    for (int w = 1; w < nwarps; ++w) acc = (tid == 5) ? fmax(acc, sh[w][tid]) : acc + sh[w][tid];
+    if (accumulate) {
+      row[tid] = (tid == 5) ? fmax(row[tid], acc) : row[tid] + acc;
+    } else {
+      row[tid] = acc;
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t block_linear() {
+  return (int64_t)blockIdx.x + (int64_t)gridDim.x * ((int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+}
+
+// Per-cell statistics contribution: {rho - 1, j_x, j_y, j_z, |u|^2/2, |u|, bad, 1}.
+template <class C>
+__device__ __forceinline__ void stats_of(C drho, const C (&j)[3], const C (&u)[3], C (&v)[8]) {
+  if (isfinite(drho) && isfinite(j[0]) && isfinite(j[1]) && isfinite(j[2])) {
+    const C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    v[0] = drho;
+    v[1] = j[0];
+    v[2] = j[1];
+    v[3] = j[2];
+    v[4] = C(0.5) * uu;
+    v[5] = sqrt(uu);
+    v[6] = C(0);
+    v[7] = C(1);
+  } else {
+    v[0] = v[1] = v[2] = v[3] = v[4] = v[5] = C(0);
+    v[6] = C(1);
+    v[7] = C(0);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------------
+template <class L, class S, int G, int SC, bool STATS>
+__global__ void __launch_bounds__(256) k_step(Params<typename Store<S>::C> p, const S* src, S* dst,
+                                              double* partials) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
+  if (x < p.nx && y < p.ny) {
+    const Nbr n = make_nbr<L>(p, x, y, z);
+    const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+    if (cls != 0) {
+      C f[L::Q];
+      gather<L, S, G>(p, src, n, cls, f);
+      C drho, j[3], rho, u[3];
+      moments<L>(f, drho, j);
+      const C gamma = p.gamma ? p.gamma[n.cell] : C(1);
+      collide<L>(p, gamma, f, drho, j, rho, u);
+      scatter<L, S, SC>(p, dst, n, cls, f, rho);
+      if (STATS) stats_of(drho, j, u, sv);
+    }
+  }
+  if (STATS) block_reduce_row(sv, partials + 8 * block_linear(), false);
+}
+
+// Canonical f(t) = f_shifted + w in double ([q][cells]); non-fluid cells 0.
+template <class L, class S, int G>
+__global__ void __launch_bounds__(256) k_to_f64(Params<typename Store<S>::C> p, const S* src, double* out) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
+  const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+  const size_t N = (size_t)p.ncell;
+  if (cls == 0) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) out[i * N + n.cell] = 0.0;
+    return;
+  }
+  C f[L::Q];
+  gather<L, S, G>(p, src, n, cls, f);
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) out[i * N + n.cell] = (double)f[i] + L::w(i);
+}
+
+template <class L, class S, int G>
+__global__ void __launch_bounds__(256) k_moments(Params<typename Store<S>::C> p, const S* src, double* rho_out,
+                                                 double* u_out) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
+  const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+  const size_t N = (size_t)p.ncell;
+  double r = 0.0, u[3] = {0.0, 0.0, 0.0};
+  if (cls != 0) {
+    C f[L::Q];
+    gather<L, S, G>(p, src, n, cls, f);
+    C drho, j[3];
+    moments<L>(f, drho, j);
+    const C rho = C(1) + drho;
+    r = (double)rho;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u[d] = (double)((j[d] + p.half_force[d]) / rho);
+  }
+  if (rho_out) rho_out[n.cell] = r;
+  if (u_out) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u_out[d * N + n.cell] = u[d];
+  }
+}
+
+template <class L, class S, int G>
+__global__ void __launch_bounds__(256) k_stats(Params<typename Store<S>::C> p, const S* src, double* partials) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
+  if (x < p.nx && y < p.ny) {
+    const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
+    const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+    if (cls != 0) {
+      C f[L::Q];
+      gather<L, S, G>(p, src, n, cls, f);
+      C drho, j[3];
+      moments<L>(f, drho, j);
+      const C rho = C(1) + drho;
+      C u[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) u[d] = (j[d] + p.half_force[d]) / rho;
+      stats_of(drho, j, u, sv);
+    }
+  }
+  block_reduce_row(sv, partials + 8 * block_linear(), false);
+}
+
+// Stored (shifted) populations from canonical double populations, own slots.
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_from_f64(Params<typename Store<S>::C> p, const double* f, S* dst) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const int cell = (blockIdx.z * p.ny + y) * p.nx + x;
+  const size_t N = (size_t)p.ncell;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + i * N + cell, (typename Store<S>::C)(f[i * N + cell] - L::w(i)));
+}
+
+// Equilibrium initialisation f = f^eq(rho, u) (rho, u nullable: 1, 0).
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_init_eq(Params<typename Store<S>::C> p, const double* rho_in,
+                                                 const double* u_in, S* dst) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const int cell = (blockIdx.z * p.ny + y) * p.nx + x;
+  const size_t N = (size_t)p.ncell;
+  const C rho = rho_in ? (C)rho_in[cell] : C(1);
+  const C drho = rho_in ? (C)(rho_in[cell] - 1.0) : C(0);
+  C u[3] = {C(0), C(0), C(0)};
+  if (u_in) {
+#pragma unroll
+    for (int d = 0; d < L::DIM; ++d) u[d] = (C)u_in[d * N + cell];
+  }
+  const C usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const C cu = L::c(i, 0) * u[0] + L::c(i, 1) * u[1] + L::c(i, 2) * u[2];
+    const C feq = (C)L::w(i) * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * usq));
+    Store<S>::st(dst + i * N + cell, feq);
+  }
+}
+
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_perturb(Params<typename Store<S>::C> p, const double* df, S* dst) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const int cell = (blockIdx.z * p.ny + y) * p.nx + x;
+  if (!p.all_fluid && p.cls[cell] == 0) return;
+  const size_t N = (size_t)p.ncell;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    S* q = dst + i * N + cell;
+    Store<S>::st(q, (C)((double)Store<S>::ld(q) + df[i * N + cell]));
+  }
+}
+
+// Rewrite a state in representation G as PRE (own slots) into another buffer.
+template <class L, class S, int G>
+__global__ void __launch_bounds__(256) k_materialize(Params<typename Store<S>::C> p, const S* src, S* dst) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= p.nx || y >= p.ny) return;
+  const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
+  const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+  if (cls == 0) return;
+  C f[L::Q];
+  gather<L, S, G>(p, src, n, cls, f);
+  const size_t N = (size_t)p.ncell;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + i * N + n.cell, f[i]);
+}
+
+// ---------------------------------------------------------------------------------
+// Adjoint.  One reverse step maps lam^{n+1} (adjoint of the pre-collision state
+// f(n+1), own slots) to lam^n, given f(n):
+//   lam*_i(x) = lam^{n+1}_i(x + c_i)  (fluid neighbour)  |  lam^{n+1}_opp(i)(x)  (wall link)
+//   lam^n_i   = (1 - omega) lam*_i + omega A + (gamma/rho) B.(c_i - u) + D
+// with mu_k = w_k lam*_k and its moments m0 = sum mu, m1 = sum mu c, m2 = sum mu c c:
+//   A = m0 (1 - 1.5 u'.u') + 3 m1.u' + 4.5 u'.m2.u'                (= sum lam*_k f^eq_k / rho)
+//   B = omega rho (3 m1 + 9 m2 u' - 3 m0 u') + (1 - omega/2)(9 m2 F - 3 m0 F)
+//   D = sum over moving-wall links of lam*_i (-6 w_i c_i.u_w)      (density in the wall term)
+// and the gradient contributions
+//   dL/dgamma(x) += B.u,
+//   dL/domega    += -sum lam*_k f_k + rho A - (3 m1.F - 3 m0 u'.F + 9 u'.m2.F)/2.
+// ---------------------------------------------------------------------------------
+template <class S>
+struct LambdaOf {
+  using T = float;
+};
+template <>
+struct LambdaOf<double> {
+  using T = double;
+};
+
+template <class L, class S, int G>
+__global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p, const S* state,
+                                                 const typename LambdaOf<S>::T* __restrict__ lam_in,
+                                                 typename LambdaOf<S>::T* __restrict__ lam_out,
+                                                 double* dgamma, double* partials) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const size_t N = (size_t)p.ncell;
+  C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
+  if (x < p.nx && y < p.ny) {
+    const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
+    const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+    if (cls != 0) {
+      // lam* = S^T lam^{n+1}
+      C ls[L::Q];
+      C direct = C(0);
+      if (cls == 1) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+          ls[i] = (C)lam_in[i * N + n.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))];
+      } else {
+        const uint32_t m = p.wmask[n.cell];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          if (i != 0 && (m & (1u << opp<L>(i)))) {
+            ls[i] = (C)lam_in[opp<L>(i) * N + n.cell];
+            if (p.moving) {
+              const int wm = link_material(p, n, L::c(i, 0), L::c(i, 1), L::c(i, 2));
+              if (wm >= 3) direct -= ls[i] * wall_term<L>(p, i, wm);
+            }
+          } else {
+            ls[i] = (C)lam_in[i * N + n.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))];
+          }
+        }
+      }
+      // forward state f(n)
+      C f[L::Q];
+      gather<L, S, G>(p, state, n, cls, f);
+      C drho, j[3];
+      moments<L>(f, drho, j);
+      const C rho = C(1) + drho;
+      const C inv = C(1) / rho;
+      const C gamma = p.gamma ? p.gamma[n.cell] : C(1);
+      C u[3], up[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        u[d] = (j[d] + p.half_force[d]) * inv;
+        up[d] = gamma * u[d];
+      }
+      // moments of mu_k = w_k lam*_k
+      C m0 = C(0), m1[3] = {C(0), C(0), C(0)};
+      C m2[3][3] = {{C(0), C(0), C(0)}, {C(0), C(0), C(0)}, {C(0), C(0), C(0)}};
+      C lf = C(0);
+#pragma unroll
+      for (int k = 0; k < L::Q; ++k) {
+        const C mu = (C)L::w(k) * ls[k];
+        m0 += mu;
+        lf += ls[k] * f[k];
+#pragma unroll
+        for (int a = 0; a < L::DIM; ++a) {
+          if (L::c(k, a) == 1) m1[a] += mu;
+          if (L::c(k, a) == -1) m1[a] -= mu;
+#pragma unroll
+          for (int b = a; b < L::DIM; ++b) {
+            const int cc = L::c(k, a) * L::c(k, b);
+            if (cc == 1) m2[a][b] += mu;
+            if (cc == -1) m2[a][b] -= mu;
+          }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < a; ++b) m2[a][b] = m2[b][a];
+      const C om = p.omega;
+      const C gf = C(1) - C(0.5) * om;
+      C m2u[3], m2F[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        m2u[a] = m2[a][0] * up[0] + m2[a][1] * up[1] + m2[a][2] * up[2];
+        m2F[a] = m2[a][0] * p.force[0] + m2[a][1] * p.force[1] + m2[a][2] * p.force[2];
+      }
+      const C usq = up[0] * up[0] + up[1] * up[1] + up[2] * up[2];
+      const C m1u = m1[0] * up[0] + m1[1] * up[1] + m1[2] * up[2];
+      const C um2u = up[0] * m2u[0] + up[1] * m2u[1] + up[2] * m2u[2];
+      const C A = m0 * (C(1) - C(1.5) * usq) + C(3) * m1u + C(4.5) * um2u;
+      C B[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        B[a] = om * rho * (C(3) * m1[a] + C(9) * m2u[a] - C(3) * m0 * up[a]) +
+               gf * (C(9) * m2F[a] - C(3) * m0 * p.force[a]);
+      const C Bu = B[0] * u[0] + B[1] * u[1] + B[2] * u[2];
+      const C gi = gamma * inv;
+      const C base = om * A - gi * Bu + direct;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        C Bc = C(0);
+#pragma unroll
+        for (int a = 0; a < L::DIM; ++a) {
+          if (L::c(i, a) == 1) Bc += B[a];
+          if (L::c(i, a) == -1) Bc -= B[a];
+        }
+        lam_out[i * N + n.cell] = (typename LambdaOf<S>::T)((C(1) - om) * ls[i] + base + gi * Bc);
+      }
+      if (dgamma) dgamma[n.cell] += (double)Bu;
+      // dL/domega: -sum lam* f (unshifted f = shifted + w, so -lf - m0) + rho A - G/2
+      const C m1F = m1[0] * p.force[0] + m1[1] * p.force[1] + m1[2] * p.force[2];
+      const C uF = up[0] * p.force[0] + up[1] * p.force[1] + up[2] * p.force[2];
+      const C uM2F = up[0] * m2F[0] + up[1] * m2F[1] + up[2] * m2F[2];
+      const C src_moment = C(3) * m1F - C(3) * m0 * uF + C(9) * uM2F;
+      sv[0] = -lf - m0 + rho * A - C(0.5) * src_moment;
+    }
+  }
+  block_reduce_row(sv, partials + 8 * block_linear(), true);
+}
+
+// Objective (mean u[comp] over fluid cells of a plane) and its gradient seed
+// lam^N_i(x) = (c_i[comp] - u[comp]) / (rho M) on those cells, 0 elsewhere.
+template <class L, class S, int G>
+__global__ void __launch_bounds__(256) k_loss_seed(Params<typename Store<S>::C> p, const S* src, int axis,
+                                                   int index, int comp, double inv_count,
+                                                   typename LambdaOf<S>::T* lam, double* partials) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const size_t N = (size_t)p.ncell;
+  C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
+  if (x < p.nx && y < p.ny) {
+    const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
+    const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+    const int coord = axis == 0 ? x : (axis == 1 ? y : (int)blockIdx.z);
+    if (cls != 0 && coord == index) {
+      C f[L::Q];
+      gather<L, S, G>(p, src, n, cls, f);
+      C drho, j[3];
+      moments<L>(f, drho, j);
+      const C rho = C(1) + drho;
+      const C jc = comp == 0 ? j[0] : (comp == 1 ? j[1] : j[2]);
+      const C fc = comp == 0 ? p.half_force[0] : (comp == 1 ? p.half_force[1] : p.half_force[2]);
+      const C uc = (jc + fc) / rho;
+      sv[0] = uc;
+      const C scale = (C)inv_count / rho;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const int ci = comp == 0 ? L::c(i, 0) : (comp == 1 ? L::c(i, 1) : L::c(i, 2));
+        lam[i * N + n.cell] = (typename LambdaOf<S>::T)(((C)ci - uc) * scale);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) lam[i * N + n.cell] = 0;
+    }
+  }
+  block_reduce_row(sv, partials + 8 * block_linear(), false);
+}
+
+// ---------------------------------------------------------------------------------
+// Host launchers (dispatch run-time pattern choices to template instances).
+// ---------------------------------------------------------------------------------
+template <class L, class S>
+struct Launch {
+  using C = typename Store<S>::C;
+  using T = typename LambdaOf<S>::T;
+
+  static Params<C> params(const HostParams& h) {
+    Params<C> p = to_params<C>(h);
+    p.all_fluid = h.cls == nullptr ? 1 : 0;
+    return p;
+  }
+
+  template <int G, int SC, bool STATS>
+  static cudaError_t step_t(const HostParams& h, const void* src, void* dst, double* partials) {
+    Grid g = make_grid(h.nx, h.ny, h.nz);
+    k_step<L, S, G, SC, STATS><<<g.grid, g.block, 0, h.stream>>>(
+        params(h), static_cast<const S*>(src), static_cast<S*>(dst), partials);
+    return cudaGetLastError();
+  }
+  template <int G, int SC>
+  static cudaError_t step_s(const HostParams& h, bool stats, const void* src, void* dst,
+                            double* partials) {
+    return stats ? step_t<G, SC, true>(h, src, dst, partials)
+                 : step_t<G, SC, false>(h, src, dst, partials);
+  }
+  static cudaError_t step(const HostParams& h, int gather, int scatter, bool stats,
+                          const void* src, void* dst, double* partials) {
+    if (gather == G_OWN && scatter == S_OWN) return step_s<G_OWN, S_OWN>(h, stats, src, dst, partials);
+    if (gather == G_PULL && scatter == S_OWN) return step_s<G_PULL, S_OWN>(h, stats, src, dst, partials);
+    if (gather == G_PULL_SWAP && scatter == S_OWN)
+      return step_s<G_PULL_SWAP, S_OWN>(h, stats, src, dst, partials);
+    if (gather == G_OWN && scatter == S_OWN_SWAP)
+      return step_s<G_OWN, S_OWN_SWAP>(h, stats, src, dst, partials);
+    if (gather == G_PULL && scatter == S_OWN_SWAP)
+      return step_s<G_PULL, S_OWN_SWAP>(h, stats, src, dst, partials);
+    if (gather == G_PULL_SWAP && scatter == S_PUSH)
+      return step_s<G_PULL_SWAP, S_PUSH>(h, stats, src, dst, partials);
+    return cudaErrorInvalidValue;
+  }
+
+#define OLB_BY_GATHER(KERNEL, ...)                                                        \
+  do {                                                                                    \
+    Grid g = make_grid(h.nx, h.ny, h.nz);                                                 \
+    if (gather == G_OWN)                                                                  \
+      KERNEL<L, S, G_OWN><<<g.grid, g.block, 0, h.stream>>>(params(h), __VA_ARGS__);      \
+    else if (gather == G_PULL)                                                            \
+      KERNEL<L, S, G_PULL><<<g.grid, g.block, 0, h.stream>>>(params(h), __VA_ARGS__);     \
+    else if (gather == G_PULL_SWAP)                                                       \
+      KERNEL<L, S, G_PULL_SWAP><<<g.grid, g.block, 0, h.stream>>>(params(h), __VA_ARGS__); \
+    else                                                                                  \
+      return cudaErrorInvalidValue;                                                       \
+    return cudaGetLastError();                                                            \
+  } while (0)
+
+  static cudaError_t to_f64(const HostParams& h, int gather, const void* src, double* f) {
+    OLB_BY_GATHER(k_to_f64, static_cast<const S*>(src), f);
+  }
+  static cudaError_t moments(const HostParams& h, int gather, const void* src, double* rho,
+                             double* u) {
+    OLB_BY_GATHER(k_moments, static_cast<const S*>(src), rho, u);
+  }
+  static cudaError_t stats(const HostParams& h, int gather, const void* src, double* partials) {
+    OLB_BY_GATHER(k_stats, static_cast<const S*>(src), partials);
+  }
+  static cudaError_t materialize(const HostParams& h, int gather, const void* src, void* dst) {
+    OLB_BY_GATHER(k_materialize, static_cast<const S*>(src), static_cast<S*>(dst));
+  }
+  static cudaError_t loss_seed(const HostParams& h, int gather, const void* src, int axis,
+                               int index, int comp, double inv_count, void* lam,
+                               double* partials) {
+    OLB_BY_GATHER(k_loss_seed, static_cast<const S*>(src), axis, index, comp, inv_count,
+                  static_cast<T*>(lam), partials);
+  }
+  static cudaError_t adjoint(const HostParams& h, int gather, const void* state,
+                             const void* lam_in, void* lam_out, double* dgamma,
+                             double* partials) {
+    if (gather == G_PULL_SWAP) return cudaErrorInvalidValue;
+    OLB_BY_GATHER(k_adjoint, static_cast<const S*>(state), static_cast<const T*>(lam_in),
+                  static_cast<T*>(lam_out), dgamma, partials);
+  }
+#undef OLB_BY_GATHER
+
+  static cudaError_t from_f64(const HostParams& h, const double* f, void* dst) {
+    Grid g = make_grid(h.nx, h.ny, h.nz);
+    k_from_f64<L, S><<<g.grid, g.block, 0, h.stream>>>(params(h), f, static_cast<S*>(dst));
+    return cudaGetLastError();
+  }
+  static cudaError_t init_eq(const HostParams& h, const double* rho, const double* u, void* dst) {
+    Grid g = make_grid(h.nx, h.ny, h.nz);
+    k_init_eq<L, S><<<g.grid, g.block, 0, h.stream>>>(params(h), rho, u, static_cast<S*>(dst));
+    return cudaGetLastError();
+  }
+  static cudaError_t perturb(const HostParams& h, const double* df, void* dst) {
+    Grid g = make_grid(h.nx, h.ny, h.nz);
+    k_perturb<L, S><<<g.grid, g.block, 0, h.stream>>>(params(h), df, static_cast<S*>(dst));
+    return cudaGetLastError();
+  }
+
+  static const KernelTable* table() {
+    static const KernelTable t = {L::Q,       sizeof(S), sizeof(T), &step,    &to_f64,
+                                  &moments,   &stats,    &from_f64, &init_eq, &perturb,
+                                  &materialize, &adjoint, &loss_seed};
+    return &t;
+  }
+};
+
+}  // namespace olb

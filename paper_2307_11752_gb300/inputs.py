@@ -54,15 +54,22 @@ def periodic_box(nx: int, ny: int, nz: int = 1) -> np.ndarray:
 
 
 def cavity(n: int, dim: int = 3) -> np.ndarray:
-    """Lid-driven cavity: fluid inside, no-slip walls on the faces, the whole top
-    plane y = n-1 (edges and corners included) is the moving lid (material 3)."""
-    nz = n if dim == 3 else 1
-    m = np.full((nz, n, n), WALL, np.uint8)
-    if dim == 3:
+    """Lid-driven cubic (square) cavity of n cells per side: fluid inside, no-slip
+    walls on the faces, the whole top plane y = n-1 (edges and corners included)
+    is the moving lid (material 3)."""
+    return cavity_box(n, n, n if dim == 3 else 1)
+
+
+def cavity_box(nx: int, ny: int, nz: int) -> np.ndarray:
+    """Box cavity of any size: fluid inside, no-slip walls on the faces, the whole
+    top plane y = ny-1 is the moving lid (material 3).  nz == 1 gives the 2D cavity
+    (walls on x and y only)."""
+    m = np.full((nz, ny, nx), WALL, np.uint8)
+    if nz > 1:
         m[1:-1, 1:-1, 1:-1] = FLUID
     else:
         m[:, 1:-1, 1:-1] = FLUID
-    m[:, n - 1, :] = LID
+    m[:, ny - 1, :] = LID
     return m
 
 
@@ -115,17 +122,18 @@ def tgv2d_velocity(n: int, u0: float, nu: float, t: float, nz: int = 1) -> np.nd
     return tgv2d(n, u0, nz)[1] * math.exp(-2.0 * nu * k * k * t)
 
 
-def tgv3d(n: int, u0: float):
+def tgv3d(n: int, u0: float, xp=np, **kw):
     """Classical 3D Taylor-Green vortex in a periodic n^3 box, k = 2 pi / n:
     u = u0 sin kx cos ky cos kz, v = -u0 cos kx sin ky cos kz, w = 0,
-    p - p0 = (u0^2/16)(cos 2kx + cos 2ky)(cos 2kz + 2), rho = 1 + 3 (p - p0)."""
+    p - p0 = (u0^2/16)(cos 2kx + cos 2ky)(cos 2kz + 2), rho = 1 + 3 (p - p0).
+    ``xp`` is numpy (default) or torch (then ``kw`` may give ``device=``)."""
     k = 2.0 * math.pi / n
-    x = np.arange(n, dtype=np.float64)
-    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
-    u = np.zeros((3, n, n, n))
-    u[0] = u0 * np.sin(k * X) * np.cos(k * Y) * np.cos(k * Z)
-    u[1] = -u0 * np.cos(k * X) * np.sin(k * Y) * np.cos(k * Z)
-    p = (u0 * u0 / 16.0) * (np.cos(2 * k * X) + np.cos(2 * k * Y)) * (np.cos(2 * k * Z) + 2.0)
+    x = xp.arange(n, dtype=xp.float64, **kw)
+    Z, Y, X = xp.meshgrid(x, x, x, indexing="ij")
+    ux = u0 * xp.sin(k * X) * xp.cos(k * Y) * xp.cos(k * Z)
+    uy = -u0 * xp.cos(k * X) * xp.sin(k * Y) * xp.cos(k * Z)
+    u = xp.stack([ux, uy, xp.zeros_like(ux)])
+    p = (u0 * u0 / 16.0) * (xp.cos(2 * k * X) + xp.cos(2 * k * Y)) * (xp.cos(2 * k * Z) + 2.0)
     return 1.0 + 3.0 * p, u
 
 
