@@ -110,7 +110,7 @@ def test_autograd_function(olb):
     g.set_bgk(case.tau)
     g.set_populations(f0)
     l2, dg, dtau = g.adjoint_run(15, 4, obj)
-    assert float(loss) == l2
+    assert float(loss.detach()) == l2
     assert torch.equal(gamma.grad, dg.view_as(gamma))
     assert float(tau.grad) == dtau
     g.close()

@@ -110,7 +110,7 @@ def test_tiny_and_degenerate_lattices(oracle, olb):
     # one-cell-wide periodic channel (Poiseuille set-up), D2Q9 and D3Q19
     for d, shape in ((0, (1, 11, 1)), (1, (1, 9, 2))):
         m = I.plates(shape[0], shape[1], shape[2])
-        case = Case(d, m, 1 | 4, 0.9, force=(1e-5, 0, 0))
+        case = Case(d, m, 1 if d == 0 else 1 | 4, 0.9, force=(1e-5, 0, 0))
         _compare(oracle, case, 33, "f64", "pull")
         _compare(oracle, case, 33, "f64", "aa")
     # no periodic axis and no wall cells: the domain edge itself bounces back
