@@ -30,6 +30,12 @@
 
 #include "olb_internal.h"
 
+// Resident blocks of 256 threads per SM that the step kernel is compiled for
+// (bounds its registers: 65536 / (256 * blocks)).
+#ifndef OLB_STEP_MIN_BLOCKS
+#define OLB_STEP_MIN_BLOCKS 3
+#endif
+
 namespace olb {
 
 // ---------------------------------------------------------------------------------
@@ -85,11 +91,15 @@ struct Store<float> {
   __device__ static C ld(const float* p) { return *p; }
   __device__ static void st(float* p, C v) { *p = v; }
 };
+// FP16 holds (f - w) * 2^12: an exact power-of-two scale that moves deviations
+// down to ~1e-8 out of FP16's subnormal range (normal range starts at 6.1e-5);
+// deviations up to 16 stay finite, far beyond any stable state.
 template <>
 struct Store<__half> {
   using C = float;
-  __device__ static C ld(const __half* p) { return __half2float(*p); }
-  __device__ static void st(__half* p, C v) { *p = __float2half_rn(v); }
+  static constexpr float kScale = 4096.0f, kInvScale = 1.0f / 4096.0f;
+  __device__ static C ld(const __half* p) { return __half2float(*p) * kInvScale; }
+  __device__ static void st(__half* p, C v) { *p = __float2half_rn(v * kScale); }
 };
 template <>
 struct Store<__nv_bfloat16> {
@@ -199,20 +209,39 @@ __device__ __forceinline__ C wall_term(const Params<C>& p, int i, int m) {
   return (C)(6.0 * L::w(i) * cu);
 }
 
-// Pull form: f_i(x) from slot i (G_PULL) or slot opp(i) (G_PULL_SWAP) of x - c_i,
-// with halfway bounce-back on wall links.
+// Gather f(t) of one cell (shifted values, compute type) from a buffer in
+// representation G, in two parts so that the bulk loads never wait for the cell
+// class: gather_bulk reads every population as if all links were fluid (indices
+// are wrapped, so always inside the buffer); gather_walls then replaces the
+// populations of wall links (cells of class 2 only).
+//   G_OWN        f_i(x) = slot i of x
+//   G_PULL       f_i(x) = slot i of x - c_i;        wall link: slot opp(i) of x
+//                (+ 6 w_i rho_x c_i.u_w on a moving wall, rho_x from x's own slots)
+//   G_PULL_SWAP  f_i(x) = slot opp(i) of x - c_i;   wall link: slot i of x, which
+//                already holds the bounced value (moving-wall term applied by the
+//                S_OWN_SWAP scatter that wrote it)
+// ---------------------------------------------------------------------------------
 template <class L, class S, int G>
-__device__ __forceinline__ void gather_links(const Params<typename Store<S>::C>& p, const S* src,
-                                             const Nbr& n, int cls,
-                                             typename Store<S>::C (&f)[L::Q]) {
-  using C = typename Store<S>::C;
+__device__ __forceinline__ void gather_bulk(const Params<typename Store<S>::C>& p, const S* src,
+                                            const Nbr& n, typename Store<S>::C (&f)[L::Q]) {
   const size_t N = (size_t)p.ncell;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const int slot = (G == G_PULL) ? i : opp<L>(i);
-    f[i] = Store<S>::ld(src + slot * N + n.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
+    if constexpr (G == G_OWN) {
+      f[i] = Store<S>::ld(src + i * N + n.cell);
+    } else {
+      const int slot = (G == G_PULL) ? i : opp<L>(i);
+      f[i] = Store<S>::ld(src + slot * N + n.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
+    }
   }
-  if (cls == 2) {
+}
+
+template <class L, class S, int G>
+__device__ __forceinline__ void gather_walls(const Params<typename Store<S>::C>& p, const S* src,
+                                             const Nbr& n, typename Store<S>::C (&f)[L::Q]) {
+  using C = typename Store<S>::C;
+  if constexpr (G != G_OWN) {
+    const size_t N = (size_t)p.ncell;
     const uint32_t m = p.wmask[n.cell];
     C rho_x = C(0);
     bool have_rho = false;
@@ -222,7 +251,7 @@ __device__ __forceinline__ void gather_links(const Params<typename Store<S>::C>&
         // halfway bounce-back: the population that left this cell towards the wall
         const int own = (G == G_PULL) ? opp<L>(i) : i;
         C v = Store<S>::ld(src + own * N + n.cell);
-        if (p.moving) {
+        if (G == G_PULL && p.moving) {
           const int wm = link_material(p, n, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
           if (wm >= 3) {
             if (!have_rho) {
@@ -240,21 +269,12 @@ __device__ __forceinline__ void gather_links(const Params<typename Store<S>::C>&
   }
 }
 
-// ---------------------------------------------------------------------------------
-// Gather f(t) of one cell (shifted values, compute type) from a buffer in
-// representation G.
-// ---------------------------------------------------------------------------------
 template <class L, class S, int G>
 __device__ __forceinline__ void gather(const Params<typename Store<S>::C>& p, const S* src,
                                        const Nbr& n, int cls,
                                        typename Store<S>::C (&f)[L::Q]) {
-  if constexpr (G == G_OWN) {
-    const size_t N = (size_t)p.ncell;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) f[i] = Store<S>::ld(src + i * N + n.cell);
-  } else {
-    gather_links<L, S, G>(p, src, n, cls, f);
-  }
+  gather_bulk<L, S, G>(p, src, n, f);
+  if (cls == 2) gather_walls<L, S, G>(p, src, n, f);
 }
 
 // ---------------------------------------------------------------------------------
@@ -348,8 +368,25 @@ __device__ __forceinline__ void scatter(const Params<typename Store<S>::C>& p, S
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + i * N + n.cell, f[i]);
   } else if (SC == S_OWN_SWAP) {
+    // f*_i(x) goes to slot opp(i) of x.  When x + c_i is a moving wall, that slot is
+    // read back only by x itself (as its bounced population f_opp(i)(x, t+1)), so
+    // the wall term is applied here, with this collision's density, instead of by
+    // the next (in-place) step, whose neighbours overwrite x's other slots.
+    if (cls == 2 && p.moving) {
+      const uint32_t m = p.wmask[n.cell];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + opp<L>(i) * N + n.cell, f[i]);
+      for (int i = 0; i < L::Q; ++i) {
+        C v = f[i];
+        if (i != 0 && (m & (1u << opp<L>(i)))) {
+          const int wm = link_material(p, n, L::c(i, 0), L::c(i, 1), L::c(i, 2));
+          if (wm >= 3) v -= rho * wall_term<L>(p, i, wm);
+        }
+        Store<S>::st(dst + opp<L>(i) * N + n.cell, v);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + opp<L>(i) * N + n.cell, f[i]);
+    }
   } else {  // S_PUSH: f*_i goes to slot i of x + c_i, or bounces back into slot opp(i) of x
     if (cls == 1) {
 #pragma unroll
@@ -437,7 +474,7 @@ __device__ __forceinline__ void stats_of(C drho, const C (&j)[3], const C (&u)[3
 // Kernels
 // ---------------------------------------------------------------------------------
 template <class L, class S, int G, int SC, bool STATS>
-__global__ void __launch_bounds__(256) k_step(Params<typename Store<S>::C> p, const S* src, S* dst,
+__global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typename Store<S>::C> p, const S* src, S* dst,
                                               double* partials) {
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -446,14 +483,19 @@ __global__ void __launch_bounds__(256) k_step(Params<typename Store<S>::C> p, co
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
   if (x < p.nx && y < p.ny) {
     const Nbr n = make_nbr<L>(p, x, y, z);
+    // The class byte and the populations are loaded together: the population
+    // loads do not depend on the class (wrapped indices are valid for every cell),
+    // so one memory latency covers both.  Non-fluid cells compute on whatever
+    // their slots hold and store nothing.
     const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+    C f[L::Q];
+    gather_bulk<L, S, G>(p, src, n, f);
+    const C gamma = p.gamma ? p.gamma[n.cell] : C(1);
+    if (cls == 2) gather_walls<L, S, G>(p, src, n, f);
+    C drho, j[3], rho, u[3];
+    moments<L>(f, drho, j);
+    collide<L>(p, gamma, f, drho, j, rho, u);
     if (cls != 0) {
-      C f[L::Q];
-      gather<L, S, G>(p, src, n, cls, f);
-      C drho, j[3], rho, u[3];
-      moments<L>(f, drho, j);
-      const C gamma = p.gamma ? p.gamma[n.cell] : C(1);
-      collide<L>(p, gamma, f, drho, j, rho, u);
       scatter<L, S, SC>(p, dst, n, cls, f, rho);
       if (STATS) stats_of(drho, j, u, sv);
     }
