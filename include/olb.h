@@ -205,6 +205,10 @@ int olb_counters(olb_handle h, int64_t* time, int64_t* kernel_launches);
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* olb_last_error(void);
 
+/* Static description of this build: target architecture and the compile-time
+ * kernel configuration (for logs and benchmark records). */
+const char* olb_build_info(void);
+
 #ifdef __cplusplus
 }
 #endif

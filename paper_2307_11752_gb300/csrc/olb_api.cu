@@ -95,6 +95,23 @@ struct DevBuf {
   }
 };
 
+// Elements between two population planes.  Planes are padded so that their
+// starting addresses do not share all low address bits (a power-of-two lattice,
+// such as 128^3, would otherwise put the 19 loads of a warp at the same offset
+// modulo 2^23 bytes), keeping 256-byte alignment of every plane.
+// Row-group mapping of the paired step kernel (see k_step_pair).
+#ifndef OLB_ROW_GROUPS
+#define OLB_ROW_GROUPS 0
+#endif
+
+#ifndef OLB_PLANE_PAD
+#define OLB_PLANE_PAD 256
+#endif
+int plane_pitch(int64_t cells) {
+  const int64_t aligned = (cells + 63) / 64 * 64;
+  return (int)(aligned + OLB_PLANE_PAD);
+}
+
 const KernelTable* table_for(int d, int t) {
   static const KernelTable* (*tables[2][4])() = {
       {table_d2q9_f64, table_d2q9_f32, table_d2q9_f16, table_d2q9_bf16},
@@ -113,49 +130,77 @@ bool is_device_pointer(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Lattice tables for host-side geometry processing (same tables as the kernels).
+// Cell classes and link masks from the material numbers (same tables as the
+// kernels).  cls: 0 non-fluid, 1 fluid with only fluid neighbours, 2 fluid with a
+// non-fluid neighbour cell, 3 fluid with a link leaving the domain along a
+// non-periodic axis.  wmask bit i: x - c_i is not fluid (or outside); pmask bit
+// i: x + c_i is a non-fluid cell inside the domain.
 template <class L>
 void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, uint8_t* cls,
-                uint32_t* wmask, bool* moving, bool* any_wall) {
+                uint32_t* wmask, uint32_t* pmask, uint32_t* word, bool* moving, bool* any_wall,
+                bool* outside_links) {
   *moving = false;
   *any_wall = false;
+  *outside_links = false;
   const int e[3] = {nx, ny, nz};
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         const int64_t c = ((int64_t)z * ny + y) * nx + x;
         wmask[c] = 0;
+        pmask[c] = 0;
+        word[c] = 0;
         if (mat[c] != OLB_MAT_FLUID) {
           cls[c] = 0;
           *any_wall = true;
-          continue;
-        }
-        uint32_t m = 0;
-        for (int i = 1; i < L::Q; ++i) {
-          int q[3] = {x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2)};
-          bool inside = true;
-          for (int a = 0; a < 3; ++a) {
-            if (q[a] < 0 || q[a] >= e[a]) {
-              if (periodic & (1u << a)) {
-                q[a] = (q[a] + e[a]) % e[a];
-              } else {
-                inside = false;
+          uint32_t nb = 0;  // bit k: x + c_k is a fluid cell
+          for (int k = 1; k < L::Q; ++k) {
+            int q[3] = {x + L::c(k, 0), y + L::c(k, 1), z + L::c(k, 2)};
+            bool inside = true;
+            for (int a = 0; a < 3; ++a) {
+              if (q[a] < 0 || q[a] >= e[a]) {
+                if (periodic & (1u << a)) q[a] = (q[a] + e[a]) % e[a];
+                else inside = false;
               }
             }
+            if (inside && mat[((int64_t)q[2] * ny + q[1]) * nx + q[0]] == OLB_MAT_FLUID) nb |= 1u << k;
           }
-          if (!inside) {
-            m |= 1u << i;
-            continue;
-          }
-          const uint8_t sm = mat[((int64_t)q[2] * ny + q[1]) * nx + q[0]];
-          if (sm != OLB_MAT_FLUID) {
-            m |= 1u << i;
-            if (sm >= 3) *moving = true;
+          word[c] = nb;
+          continue;
+        }
+        bool moving_link = false;
+        uint32_t wm = 0, pm = 0;
+        bool out = false;
+        for (int i = 1; i < L::Q; ++i) {
+          for (int sgn = -1; sgn <= 1; sgn += 2) {  // -1: pull source x - c_i, +1: push target x + c_i
+            int q[3] = {x + sgn * L::c(i, 0), y + sgn * L::c(i, 1), z + sgn * L::c(i, 2)};
+            bool inside = true;
+            for (int a = 0; a < 3; ++a) {
+              if (q[a] < 0 || q[a] >= e[a]) {
+                if (periodic & (1u << a)) {
+                  q[a] = (q[a] + e[a]) % e[a];
+                } else {
+                  inside = false;
+                }
+              }
+            }
+            const uint8_t nm = inside ? mat[((int64_t)q[2] * ny + q[1]) * nx + q[0]] : (uint8_t)OLB_MAT_VOID;
+            if (!inside || nm != OLB_MAT_FLUID) {
+              if (sgn < 0) wm |= 1u << i;
+              if (sgn > 0 && inside) {
+                pm |= 1u << i;
+                if (nm >= 3) *moving = moving_link = true;
+              }
+              if (!inside) out = true;
+            }
           }
         }
-        wmask[c] = m;
-        cls[c] = m ? 2 : 1;
-        if (m) *any_wall = true;
+        wmask[c] = wm;
+        pmask[c] = pm;
+        word[c] = kWordFluid | (moving_link ? kWordMoving : 0u) | pm;
+        cls[c] = out ? 3 : (wm ? 2 : 1);
+        if (out) *outside_links = true;
+        if (wm) *any_wall = true;
       }
 }
 
@@ -166,12 +211,13 @@ void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, u
 // ---------------------------------------------------------------------------------
 struct olb_lattice {
   int desc = 0, dtype = 0, q = 0, dim = 0;
-  int nx = 0, ny = 0, nz = 0, ncell = 0;
+  int nx = 0, ny = 0, nz = 0, ncell = 0, pitch = 0;
   const KernelTable* kt = nullptr;
   cudaStream_t stream = nullptr;
   DevBuf buf[2];
   int cur = 0, repr = PRE, scheme = OLB_PULL;
-  DevBuf mat, cls, wmask, wall_u, gamma, partials, out8;
+  DevBuf mat, cls, wmask, pmask, word, wall_u, gamma, partials, out8;
+  bool outside_links = false;
   std::vector<uint8_t> h_mat;
   unsigned periodic = 0;
   bool all_fluid = false, moving = false;
@@ -180,7 +226,7 @@ struct olb_lattice {
   bool has_gamma = false;
   int64_t time = 0, launches = 0;
 
-  size_t state_bytes() const { return (size_t)q * ncell * kt->state_elem; }
+  size_t state_bytes() const { return (size_t)q * pitch * kt->state_elem; }
   size_t compute_elem() const { return dtype == OLB_F64 ? sizeof(double) : sizeof(float); }
 
   HostParams params() const {
@@ -189,6 +235,7 @@ struct olb_lattice {
     p.ny = ny;
     p.nz = nz;
     p.ncell = ncell;
+    p.pitch = pitch;
     p.periodic = periodic;
     p.cls = all_fluid ? nullptr : static_cast<const uint8_t*>(cls.p);
     p.wmask = static_cast<const uint32_t*>(wmask.p);
@@ -199,10 +246,16 @@ struct olb_lattice {
     for (int a = 0; a < 3; ++a) p.force[a] = F[a];
     p.forced = (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0) ? 1 : 0;
     p.gamma = has_gamma ? gamma.p : nullptr;
+    p.pmask = static_cast<const uint32_t*>(pmask.p);
+    p.word = static_cast<const uint32_t*>(word.p);
+    p.outside_links = outside_links ? 1 : 0;
     p.stream = stream;
     return p;
   }
-  int64_t grid_blocks() const { return make_grid(nx, ny, nz).blocks(); }
+  // blocks (= rows of partial sums) of the step kernel and of the per-cell kernels
+  int64_t step_rows() const { return make_step_grid(nx, ny, nz, dtype != OLB_F64 && pairs_ok(nx)).blocks(); }
+  int64_t cell_rows() const { return make_grid(nx, ny, nz).blocks(); }
+  int64_t grid_blocks() const { return std::max(step_rows(), cell_rows()); }
 };
 
 namespace olb {
@@ -242,6 +295,25 @@ __global__ void k_reduce_rows(const double* __restrict__ rows, int64_t n, double
     __syncthreads();
   }
   if (threadIdx.x < 8) out[threadIdx.x] = sh[0][threadIdx.x];
+}
+
+StepGrid make_step_grid(int nx, int ny, int nz, bool pairs) {
+  StepGrid g;
+  const int units = pairs ? nx / 2 : nx;  // threads needed along x
+  int shift = 5;  // 32 .. 256 threads along x
+  while (shift < 8 && (1 << shift) < units) ++shift;
+  g.tile_shift = shift;
+  const int rows = 256 >> shift;
+  g.gx = (units + (1 << shift) - 1) >> shift;
+  // paired kernel: whole rows per block when a row has 4 .. 256 pairs
+  const int P = nx / 2;
+  if (pairs && P >= 4 && P <= 256 && OLB_ROW_GROUPS) {
+    g.pair_rows = 256 / P;
+    g.row_blocks = ((int64_t)ny * nz + g.pair_rows - 1) / g.pair_rows;
+  }
+  g.gy = (ny + rows - 1) / rows;
+  g.nz = nz;
+  return g;
 }
 
 cudaError_t reduce_partials(const double* partials, int64_t rows, double* out, cudaStream_t s) {
@@ -380,6 +452,19 @@ extern "C" {
 
 const char* olb_last_error(void) { return g_err.c_str(); }
 
+#define OLB_STR2(x) #x
+#define OLB_STR(x) OLB_STR2(x)
+const char* olb_build_info(void) {
+  return "sm_103a step_min_blocks=" OLB_STR(OLB_STEP_MIN_BLOCKS) " pair_min_blocks=" OLB_STR(OLB_PAIR_MIN_BLOCKS) " pair16_min_blocks=" OLB_STR(OLB_PAIR16_MIN_BLOCKS)
+         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " row_groups=" OLB_STR(OLB_ROW_GROUPS) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
+#ifdef OLB_NO_PAIRS
+         " pairs=off"
+#else
+         " pairs=on"
+#endif
+      ;
+}
+
 int olb_set_allocator(void* (*alloc)(size_t, void*), void (*free_)(void*, void*), void* ctx) {
   std::lock_guard<std::mutex> lk(g_provider_mu);
   if (alloc && !free_) return fail(OLB_ERR_ARG, "allocator without a free function");
@@ -399,7 +484,7 @@ int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, ol
   if (nx < 1 || ny < 1 || nz < 1) return fail(OLB_ERR_ARG, "lattice sizes must be >= 1");
   if (d == OLB_D2Q9 && nz != 1) return fail(OLB_ERR_ARG, "D2Q9 requires nz == 1");
   const int64_t cells = (int64_t)nx * ny * nz;
-  if (cells > 2147483647LL) return fail(OLB_ERR_ARG, "more than 2^31 - 1 cells");
+  if (cells > 2147483647LL - 4096) return fail(OLB_ERR_ARG, "more than 2^31 - 4097 cells");
   if (nz > 65535) return fail(OLB_ERR_ARG, "nz > 65535");
   olb_lattice* h = new olb_lattice();
   h->desc = (int)d;
@@ -411,10 +496,12 @@ int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, ol
   h->ny = ny;
   h->nz = nz;
   h->ncell = (int)cells;
+  h->pitch = plane_pitch(cells);
   std::memset(h->h_wall, 0, sizeof(h->h_wall));
   int rc;
   if ((rc = h->buf[0].reserve(h->state_bytes())) || (rc = h->mat.reserve(cells)) ||
-      (rc = h->cls.reserve(cells)) || (rc = h->wmask.reserve(cells * 4)) ||
+      (rc = h->cls.reserve(cells)) || (rc = h->wmask.reserve(cells * 4)) || (rc = h->pmask.reserve(cells * 4)) ||
+      (rc = h->word.reserve(cells * 4)) ||
       (rc = h->wall_u.reserve(sizeof(h->h_wall))) ||
       (rc = ensure_partials(h, h->grid_blocks()))) {
     std::string msg = g_err;
@@ -479,19 +566,24 @@ int olb_set_material(olb_handle h, const uint8_t* material, unsigned periodic_ma
   // the current state is kept in the canonical form across the geometry change
   if ((rc = materialize(h))) return rc;
   std::vector<uint8_t> cls(n);
-  std::vector<uint32_t> wm(n);
-  bool moving = false, any_wall = false;
+  std::vector<uint32_t> wm(n), pm(n), wd(n);
+  bool moving = false, any_wall = false, outside_links = false;
   if (h->desc == OLB_D2Q9)
-    link_masks<D2Q9>(h->nx, h->ny, h->nz, periodic_mask, m.data(), cls.data(), wm.data(), &moving, &any_wall);
+    link_masks<D2Q9>(h->nx, h->ny, h->nz, periodic_mask, m.data(), cls.data(), wm.data(), pm.data(), wd.data(),
+                     &moving, &any_wall, &outside_links);
   else
-    link_masks<D3Q19>(h->nx, h->ny, h->nz, periodic_mask, m.data(), cls.data(), wm.data(), &moving, &any_wall);
+    link_masks<D3Q19>(h->nx, h->ny, h->nz, periodic_mask, m.data(), cls.data(), wm.data(), pm.data(), wd.data(),
+                      &moving, &any_wall, &outside_links);
   OLB_CUDA(cudaMemcpyAsync(h->mat.p, m.data(), n, cudaMemcpyHostToDevice, h->stream), "material upload");
   OLB_CUDA(cudaMemcpyAsync(h->cls.p, cls.data(), n, cudaMemcpyHostToDevice, h->stream), "class upload");
   OLB_CUDA(cudaMemcpyAsync(h->wmask.p, wm.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "mask upload");
+  OLB_CUDA(cudaMemcpyAsync(h->pmask.p, pm.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "mask upload");
+  OLB_CUDA(cudaMemcpyAsync(h->word.p, wd.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "word upload");
   OLB_CUDA(cudaStreamSynchronize(h->stream), "material sync");
   h->h_mat.swap(m);
   h->periodic = periodic_mask;
   h->moving = moving;
+  h->outside_links = outside_links;
   h->all_fluid = !any_wall;
   return upload_wall(h);
 }
@@ -639,7 +731,7 @@ int olb_step_stats(olb_handle h, int64_t n, double* out) {
   if (rc) return rc;
   if (n < 1) return fail(OLB_ERR_ARG, "olb_step_stats needs n >= 1");
   if (!out) return fail(OLB_ERR_ARG, "null output");
-  const int64_t rows = h->grid_blocks();
+  const int64_t rows = h->step_rows();
   if ((rc = ensure_partials(h, rows))) return rc;
   for (int64_t s = 0; s + 1 < n; ++s)
     if ((rc = step_once(h, false, nullptr))) return rc;
@@ -673,7 +765,7 @@ int olb_diagnostics(olb_handle h, double* out) {
   int rc = check(h);
   if (rc) return rc;
   if (!out) return fail(OLB_ERR_ARG, "null output");
-  const int64_t rows = h->grid_blocks();
+  const int64_t rows = h->cell_rows();
   if ((rc = ensure_partials(h, rows))) return rc;
   HostParams p = h->params();
   if ((rc = launched(h, h->kt->stats(p, gather_of(h->repr), h->buf[h->cur].p, static_cast<double*>(h->partials.p)), "diagnostics")))
@@ -721,8 +813,8 @@ int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t K, const olb_objectiv
   if (K > n_steps) K = n_steps;
   const int64_t nseg = (n_steps + K - 1) / K;
   const size_t sb = h->state_bytes();
-  const size_t lb = (size_t)h->q * h->ncell * h->kt->lambda_elem;
-  const int64_t rows = h->grid_blocks();
+  const size_t lb = (size_t)h->q * h->pitch * h->kt->lambda_elem;
+  const int64_t rows = h->cell_rows();
 
   // buffers: checkpoints, segment slots 1..K-1, two adjoint fields, gradients
   std::vector<DevBuf> ckpt(nseg), seg(K);
@@ -733,7 +825,7 @@ int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t K, const olb_objectiv
   for (int64_t k = 1; k < K; ++k)
     if ((rc = seg[k].reserve(sb))) return rc;
   if ((rc = lam[0].reserve(lb)) || (rc = lam[1].reserve(lb)) || (rc = dg.reserve((size_t)h->ncell * 8)) ||
-      (rc = part.reserve((size_t)rows * 8 * sizeof(double))) || (rc = ensure_partials(h, rows)))
+      (rc = part.reserve((size_t)rows * 8 * sizeof(double))) || (rc = ensure_partials(h, h->grid_blocks())))
     return rc;
   if (h->repr == AA_ODD && (rc = materialize(h))) return rc;
 

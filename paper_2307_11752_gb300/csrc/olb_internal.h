@@ -26,8 +26,10 @@ inline int gather_of(int repr) { return repr == PRE ? G_OWN : (repr == POST ? G_
 struct HostParams {
   int nx, ny, nz;
   int ncell;
+  int pitch;              // elements between population planes of stored fields
   unsigned periodic;
-  const uint8_t* cls;     // per cell: 0 non-fluid, 1 fluid with only fluid links, 2 fluid with wall links
+  const uint8_t* cls;     // per cell: 0 non-fluid, 1 fluid with only fluid links, 2 fluid with links to
+                          // wall cells, 3 fluid with links leaving the domain (non-periodic edge)
   const uint32_t* wmask;  // per cell: bit i set when the pull source x - c_i is not a fluid cell
   const uint8_t* mat;     // material numbers
   const double* wall_u;   // [256][4] moving-wall velocities
@@ -36,6 +38,9 @@ struct HostParams {
   double force[3];
   int forced;
   const void* gamma;      // per-cell porosity in the compute type, or nullptr
+  const uint32_t* pmask;  // per cell: bit i set when x + c_i is a non-fluid cell of the lattice
+  const uint32_t* word;   // per cell link word of the step kernel
+  int outside_links;      // some fluid cell has a link leaving the domain
   cudaStream_t stream;
 };
 
@@ -45,6 +50,23 @@ struct Grid {
   int64_t blocks() const { return (int64_t)grid.x * grid.y * grid.z; }
 };
 Grid make_grid(int nx, int ny, int nz);
+
+// Grid of the step kernel: 1D over gx * gy * nz tiles of (1 << tile_shift) threads
+// along x by (256 >> tile_shift) rows; a thread updates one cell, or two
+// neighbouring cells (x0, x0 + 1) in the paired kernel.
+struct StepGrid {
+  int gx, gy, nz, tile_shift;
+  int pair_rows = 0;    // paired kernel: rows per block (row-group mapping), 0 = tiles
+  int64_t row_blocks = 0;
+  int64_t blocks() const { return pair_rows > 0 ? row_blocks : (int64_t)gx * gy * nz; }
+};
+StepGrid make_step_grid(int nx, int ny, int nz, bool pairs);
+// The paired kernel runs for FP32-arithmetic storage types when nx is even.
+#ifdef OLB_NO_PAIRS
+inline bool pairs_ok(int) { return false; }
+#else
+inline bool pairs_ok(int nx) { return nx % 2 == 0; }
+#endif
 
 // Launchers of one (lattice, storage type) pair.  Each returns the CUDA error of
 // the launch.  `partials` receives one row of 8 doubles per block (reductions).

@@ -28,12 +28,22 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "olb_internal.h"
 
 // Resident blocks of 256 threads per SM that the step kernel is compiled for
 // (bounds its registers: 65536 / (256 * blocks)).
 #ifndef OLB_STEP_MIN_BLOCKS
-#define OLB_STEP_MIN_BLOCKS 3
+#define OLB_STEP_MIN_BLOCKS 4
+#endif
+// Same for the two-cells-per-thread step kernel (FP32 arithmetic), for FP32
+// storage and for 16-bit storage (which needs more cells in flight per byte).
+#ifndef OLB_PAIR_MIN_BLOCKS
+#define OLB_PAIR_MIN_BLOCKS 2
+#endif
+#ifndef OLB_PAIR16_MIN_BLOCKS
+#define OLB_PAIR16_MIN_BLOCKS 3
 #endif
 
 namespace olb {
@@ -74,6 +84,20 @@ __host__ __device__ constexpr int opp(int i) {
   return i == 0 ? 0 : (i <= L::HALF ? i + L::HALF : i - L::HALF);
 }
 
+// Link word of a cell, read by the step kernel together with the populations.
+//   fluid cell:  kWordFluid | [kWordMoving] | bit i for every link whose target
+//                x + c_i is a non-fluid cell of the lattice (bounce-back link)
+//   other cell:  bit i when x + c_i is a fluid cell
+constexpr uint32_t kWordFluid = 1u << 31;
+constexpr uint32_t kWordMoving = 1u << 30;  // a bounce-back link hits a moving wall
+constexpr uint32_t kWordLinks = (1u << 19) - 1;
+
+// Non-fluid cells also store zeros into the slots that no fluid neighbour fills,
+// so that every memory sector of a step's output is written in full.
+#ifndef OLB_SOLID_FILL
+#define OLB_SOLID_FILL 0
+#endif
+
 // ---------------------------------------------------------------------------------
 // Storage types: load/store with conversion to the compute type.
 // ---------------------------------------------------------------------------------
@@ -112,16 +136,26 @@ struct Store<__nv_bfloat16> {
 template <class C>
 struct Params {
   int nx, ny, nz, ncell;
+  int pitch;  // elements between population planes (>= ncell; canonical arrays use ncell)
   unsigned periodic;
   int all_fluid;  // every cell fluid and every axis periodic: no class reads
   const uint8_t* __restrict__ cls;
-  const uint32_t* __restrict__ wmask;
+  const uint32_t* __restrict__ wmask;  // per cell: bit i set when x - c_i is not a fluid cell
   const uint8_t* __restrict__ mat;
   const double* __restrict__ wall_u;  // [256][4]
   int moving;
   C omega, half_force[3], force[3];
   int forced;
   const C* __restrict__ gamma;
+  // per cell: bit i set when x + c_i is a non-fluid cell of the lattice (a wall
+  // link whose bounced population is stored in that cell)
+  const uint32_t* __restrict__ pmask;
+  // per cell link word of the step kernel (see kWordFluid)
+  const uint32_t* __restrict__ word;
+  int outside_links;  // some fluid cell has a link leaving the domain
+  // step-kernel grid: gx * gy * nz tiles of (1 << tile_shift) x (256 >> tile_shift),
+  // or, for the paired kernel with pair_rows > 0, blocks of pair_rows whole rows
+  int gx, gy, tile_shift, pair_rows;
 };
 
 template <class C>
@@ -131,6 +165,7 @@ Params<C> to_params(const HostParams& h) {
   p.ny = h.ny;
   p.nz = h.nz;
   p.ncell = h.ncell;
+  p.pitch = h.pitch;
   p.periodic = h.periodic;
   p.all_fluid = 0;
   p.cls = h.cls;
@@ -145,6 +180,14 @@ Params<C> to_params(const HostParams& h) {
   }
   p.forced = h.forced;
   p.gamma = reinterpret_cast<const C*>(h.gamma);
+  p.pmask = h.pmask;
+  p.word = h.word;
+  p.outside_links = h.outside_links;
+  const StepGrid sg = make_step_grid(h.nx, h.ny, h.nz, false);
+  p.gx = sg.gx;
+  p.gy = sg.gy;
+  p.tile_shift = sg.tile_shift;
+  p.pair_rows = 0;
   return p;
 }
 
@@ -209,22 +252,24 @@ __device__ __forceinline__ C wall_term(const Params<C>& p, int i, int m) {
   return (C)(6.0 * L::w(i) * cu);
 }
 
+// ---------------------------------------------------------------------------------
 // Gather f(t) of one cell (shifted values, compute type) from a buffer in
-// representation G, in two parts so that the bulk loads never wait for the cell
-// class: gather_bulk reads every population as if all links were fluid (indices
-// are wrapped, so always inside the buffer); gather_walls then replaces the
-// populations of wall links (cells of class 2 only).
-//   G_OWN        f_i(x) = slot i of x
-//   G_PULL       f_i(x) = slot i of x - c_i;        wall link: slot opp(i) of x
-//                (+ 6 w_i rho_x c_i.u_w on a moving wall, rho_x from x's own slots)
-//   G_PULL_SWAP  f_i(x) = slot opp(i) of x - c_i;   wall link: slot i of x, which
-//                already holds the bounced value (moving-wall term applied by the
-//                S_OWN_SWAP scatter that wrote it)
+// representation G:
+//   G_OWN        f_i(x) = slot i of x                         (state PRE)
+//   G_PULL       f_i(x) = slot i of x - c_i                   (state POST)
+//   G_PULL_SWAP  f_i(x) = slot opp(i) of x - c_i              (state AA_ODD)
+// Bounce-back needs no special case here: when x - c_i is a wall cell, the step
+// that wrote the buffer stored the bounced population (moving-wall term
+// included) in that wall cell's slot, which only x writes and only x reads (see
+// scatter).  Only links that leave the domain along a non-periodic axis have no
+// cell to hold it; cells with such links (class 3) take them from their own
+// slots in gather_outside.  Every index is wrapped, so the bulk loads are valid
+// for every cell and never wait for the cell class.
 // ---------------------------------------------------------------------------------
 template <class L, class S, int G>
 __device__ __forceinline__ void gather_bulk(const Params<typename Store<S>::C>& p, const S* src,
                                             const Nbr& n, typename Store<S>::C (&f)[L::Q]) {
-  const size_t N = (size_t)p.ncell;
+  const size_t N = (size_t)p.pitch;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     if constexpr (G == G_OWN) {
@@ -236,34 +281,30 @@ __device__ __forceinline__ void gather_bulk(const Params<typename Store<S>::C>& 
   }
 }
 
+// True when cell + (dx, dy, dz) leaves the domain along a non-periodic axis.
+template <class C>
+__device__ __forceinline__ bool outside(const Params<C>& p, const Nbr& n, int dx, int dy, int dz) {
+  const int q[3] = {n.x + dx, n.y + dy, n.z + dz};
+  const int e[3] = {p.nx, p.ny, p.nz};
+  bool out = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (!(p.periodic & (1u << a)) && (q[a] < 0 || q[a] >= e[a])) out = true;
+  return out;
+}
+
 template <class L, class S, int G>
-__device__ __forceinline__ void gather_walls(const Params<typename Store<S>::C>& p, const S* src,
-                                             const Nbr& n, typename Store<S>::C (&f)[L::Q]) {
-  using C = typename Store<S>::C;
+__device__ __forceinline__ void gather_outside(const Params<typename Store<S>::C>& p, const S* src,
+                                               const Nbr& n, typename Store<S>::C (&f)[L::Q]) {
   if constexpr (G != G_OWN) {
-    const size_t N = (size_t)p.ncell;
-    const uint32_t m = p.wmask[n.cell];
-    C rho_x = C(0);
-    bool have_rho = false;
+    const size_t N = (size_t)p.pitch;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
-      if (m & (1u << i)) {
-        // halfway bounce-back: the population that left this cell towards the wall
+      if (outside(p, n, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2))) {
+        // no-slip bounce-back at the domain edge: the population that left x
+        // towards the edge, from x's own slots
         const int own = (G == G_PULL) ? opp<L>(i) : i;
-        C v = Store<S>::ld(src + own * N + n.cell);
-        if (G == G_PULL && p.moving) {
-          const int wm = link_material(p, n, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-          if (wm >= 3) {
-            if (!have_rho) {
-              rho_x = C(1);
-#pragma unroll
-              for (int j = 0; j < L::Q; ++j) rho_x += Store<S>::ld(src + j * N + n.cell);
-              have_rho = true;
-            }
-            v += rho_x * wall_term<L>(p, i, wm);
-          }
-        }
-        f[i] = v;
+        f[i] = Store<S>::ld(src + own * N + n.cell);
       }
     }
   }
@@ -274,7 +315,7 @@ __device__ __forceinline__ void gather(const Params<typename Store<S>::C>& p, co
                                        const Nbr& n, int cls,
                                        typename Store<S>::C (&f)[L::Q]) {
   gather_bulk<L, S, G>(p, src, n, f);
-  if (cls == 2) gather_walls<L, S, G>(p, src, n, f);
+  if (cls == 3) gather_outside<L, S, G>(p, src, n, f);
 }
 
 // ---------------------------------------------------------------------------------
@@ -355,51 +396,59 @@ __device__ __forceinline__ void collide(const Params<C>& p, C gamma, C (&f)[L::Q
 }
 
 // ---------------------------------------------------------------------------------
-// Scatter post-collision values to a buffer with pattern SC.
+// Scatter post-collision values f*_i(x) to a buffer with pattern SC.
+//   S_OWN       slot i of x                         -> state POST (next gather G_PULL)
+//   S_OWN_SWAP  slot opp(i) of x                    -> state AA_ODD (next gather G_PULL_SWAP)
+//   S_PUSH      slot i of x + c_i                   -> state PRE (next gather G_OWN)
+// Halfway bounce-back (class >= 2, `pm` = links whose target x + c_i is a wall
+// cell of the lattice): the bounced population f*_i(x) - 6 w_i rho_x c_i.u_w is
+// what x will read for direction opp(i) at the next step.  S_OWN and S_OWN_SWAP
+// store it in the wall cell x + c_i, in the slot the next gather of x reads
+// there (opp(i) for G_PULL, i for G_PULL_SWAP); S_PUSH stores it in x's own
+// slot opp(i).  Links leaving the domain (class 3) bounce through x's own slots.
 // ---------------------------------------------------------------------------------
 template <class L, class S, int SC>
 __device__ __forceinline__ void scatter(const Params<typename Store<S>::C>& p, S* dst,
-                                        const Nbr& n, int cls,
+                                        const Nbr& n, int cls, uint32_t pm,
                                         const typename Store<S>::C (&f)[L::Q],
                                         typename Store<S>::C rho) {
   using C = typename Store<S>::C;
-  const size_t N = (size_t)p.ncell;
-  if (SC == S_OWN) {
+  const size_t N = (size_t)p.pitch;
+  if (SC == S_OWN || SC == S_OWN_SWAP) {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + i * N + n.cell, f[i]);
-  } else if (SC == S_OWN_SWAP) {
-    // f*_i(x) goes to slot opp(i) of x.  When x + c_i is a moving wall, that slot is
-    // read back only by x itself (as its bounced population f_opp(i)(x, t+1)), so
-    // the wall term is applied here, with this collision's density, instead of by
-    // the next (in-place) step, whose neighbours overwrite x's other slots.
-    if (cls == 2 && p.moving) {
-      const uint32_t m = p.wmask[n.cell];
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        C v = f[i];
-        if (i != 0 && (m & (1u << opp<L>(i)))) {
-          const int wm = link_material(p, n, L::c(i, 0), L::c(i, 1), L::c(i, 2));
-          if (wm >= 3) v -= rho * wall_term<L>(p, i, wm);
-        }
-        Store<S>::st(dst + opp<L>(i) * N + n.cell, v);
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + opp<L>(i) * N + n.cell, f[i]);
+    for (int i = 0; i < L::Q; ++i) {
+      const int slot = (SC == S_OWN) ? i : opp<L>(i);
+      Store<S>::st(dst + slot * N + n.cell, f[i]);
     }
-  } else {  // S_PUSH: f*_i goes to slot i of x + c_i, or bounces back into slot opp(i) of x
+    if (cls >= 2) {
+#pragma unroll
+      for (int i = 1; i < L::Q; ++i) {
+        if (pm & (1u << i)) {
+          C v = f[i];
+          if (pm & kWordMoving) {
+            const int wm = p.mat[n.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))];
+            if (wm >= 3) v -= rho * wall_term<L>(p, i, wm);
+          }
+          const int slot = (SC == S_OWN) ? opp<L>(i) : i;
+          Store<S>::st(dst + slot * N + n.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), v);
+        }
+      }
+    }
+  } else {  // S_PUSH
     if (cls == 1) {
 #pragma unroll
       for (int i = 0; i < L::Q; ++i)
         Store<S>::st(dst + i * N + n.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), f[i]);
     } else {
-      const uint32_t m = p.wmask[n.cell];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        if (i != 0 && (m & (1u << opp<L>(i)))) {
+        const bool wall = i != 0 && (pm & (1u << i));
+        const bool edge = i != 0 && cls == 3 && outside(p, n, L::c(i, 0), L::c(i, 1), L::c(i, 2));
+        // (pm carries only link bits 0..18 and kWordMoving)
+        if (wall || edge) {
           C v = f[i];
-          if (p.moving) {
-            const int wm = link_material(p, n, L::c(i, 0), L::c(i, 1), L::c(i, 2));
+          if (wall && (pm & kWordMoving)) {
+            const int wm = p.mat[n.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))];
             if (wm >= 3) v -= rho * wall_term<L>(p, i, wm);
           }
           Store<S>::st(dst + opp<L>(i) * N + n.cell, v);
@@ -473,34 +522,70 @@ __device__ __forceinline__ void stats_of(C drho, const C (&j)[3], const C (&u)[3
 // ---------------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------------
+// Zero the slots of a non-fluid cell that no fluid neighbour writes in this step
+// (its bounce-back slots are written by the neighbours).  `nb` = bit k when
+// x + c_k is fluid.  Pull (S_OWN): slot k is filled by x + c_k.  AA (S_OWN_SWAP,
+// S_PUSH): slot k is filled by, or read in this step by, x - c_k.
+template <class L, class S, int SC>
+__device__ __forceinline__ void solid_fill(const Params<typename Store<S>::C>& p, S* dst,
+                                           const Nbr& n, uint32_t nb) {
+  const size_t N = (size_t)p.pitch;
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k) {
+    const int b = (SC == S_OWN) ? k : opp<L>(k);
+    if (k == 0 || !(nb & (1u << b))) Store<S>::st(dst + k * N + n.cell, typename Store<S>::C(0));
+  }
+}
+
+// True when the cell lies on a face of the domain along a non-periodic axis.
+template <class L, class C>
+__device__ __forceinline__ bool on_edge(const Params<C>& p, int x, int y, int z) {
+  return (!(p.periodic & 1u) && (x == 0 || x == p.nx - 1)) ||
+         (!(p.periodic & 2u) && (y == 0 || y == p.ny - 1)) ||
+         (L::DIM == 3 && !(p.periodic & 4u) && (z == 0 || z == p.nz - 1));
+}
+
+// One collide-and-stream step.  Blocks tile the lattice in rows of up to 256
+// cells along x.  Each thread loads its cell's link word together with the
+// populations -- no load depends on another -- so a single memory latency covers
+// the cell; it collides and stores.  Links leaving the domain (only when some
+// fluid cell touches a non-periodic domain face) are recognised from the
+// coordinates, again without waiting for a load.
 template <class L, class S, int G, int SC, bool STATS>
-__global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typename Store<S>::C> p, const S* src, S* dst,
-                                              double* partials) {
+__global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typename Store<S>::C> p,
+                                                                  const S* src, S* dst,
+                                                                  double* partials) {
   using C = typename Store<S>::C;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
+  const int tid = threadIdx.x;
+  const int t = blockIdx.x;
+  const int tz = t / p.gx;
+  const int bx = t - tz * p.gx;
+  const int by = tz % p.gy;
+  const int z = tz / p.gy;
+  const int x = (bx << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1));
+  const int y = by * (256 >> p.tile_shift) + (tid >> p.tile_shift);
   if (x < p.nx && y < p.ny) {
     const Nbr n = make_nbr<L>(p, x, y, z);
-    // The class byte and the populations are loaded together: the population
-    // loads do not depend on the class (wrapped indices are valid for every cell),
-    // so one memory latency covers both.  Non-fluid cells compute on whatever
-    // their slots hold and store nothing.
-    const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+    const uint32_t w = p.all_fluid ? kWordFluid : p.word[n.cell];
     C f[L::Q];
     gather_bulk<L, S, G>(p, src, n, f);
     const C gamma = p.gamma ? p.gamma[n.cell] : C(1);
-    if (cls == 2) gather_walls<L, S, G>(p, src, n, f);
+    const bool edge = p.outside_links && on_edge<L>(p, x, y, z);
+    if (edge) gather_outside<L, S, G>(p, src, n, f);
     C drho, j[3], rho, u[3];
     moments<L>(f, drho, j);
     collide<L>(p, gamma, f, drho, j, rho, u);
-    if (cls != 0) {
-      scatter<L, S, SC>(p, dst, n, cls, f, rho);
+    if (w & kWordFluid) {
+      const uint32_t pm = w & (kWordLinks | kWordMoving);
+      const int cls = edge ? 3 : (pm ? 2 : 1);
+      scatter<L, S, SC>(p, dst, n, cls, pm, f, rho);
       if (STATS) stats_of(drho, j, u, sv);
+    } else if (OLB_SOLID_FILL) {
+      solid_fill<L, S, SC>(p, dst, n, w & kWordLinks);
     }
   }
-  if (STATS) block_reduce_row(sv, partials + 8 * block_linear(), false);
+  if (STATS) block_reduce_row(sv, partials + 8 * (int64_t)blockIdx.x, false);
 }
 
 // Canonical f(t) = f_shifted + w in double ([q][cells]); non-fluid cells 0.
@@ -585,7 +670,7 @@ __global__ void __launch_bounds__(256) k_from_f64(Params<typename Store<S>::C> p
   const int cell = (blockIdx.z * p.ny + y) * p.nx + x;
   const size_t N = (size_t)p.ncell;
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + i * N + cell, (typename Store<S>::C)(f[i * N + cell] - L::w(i)));
+  for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + i * (size_t)p.pitch + cell, (typename Store<S>::C)(f[i * N + cell] - L::w(i)));
 }
 
 // Equilibrium initialisation f = f^eq(rho, u) (rho, u nullable: 1, 0).
@@ -610,7 +695,7 @@ __global__ void __launch_bounds__(256) k_init_eq(Params<typename Store<S>::C> p,
   for (int i = 0; i < L::Q; ++i) {
     const C cu = L::c(i, 0) * u[0] + L::c(i, 1) * u[1] + L::c(i, 2) * u[2];
     const C feq = (C)L::w(i) * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * usq));
-    Store<S>::st(dst + i * N + cell, feq);
+    Store<S>::st(dst + i * (size_t)p.pitch + cell, feq);
   }
 }
 
@@ -625,7 +710,7 @@ __global__ void __launch_bounds__(256) k_perturb(Params<typename Store<S>::C> p,
   const size_t N = (size_t)p.ncell;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    S* q = dst + i * N + cell;
+    S* q = dst + i * (size_t)p.pitch + cell;
     Store<S>::st(q, (C)((double)Store<S>::ld(q) + df[i * N + cell]));
   }
 }
@@ -642,7 +727,7 @@ __global__ void __launch_bounds__(256) k_materialize(Params<typename Store<S>::C
   if (cls == 0) return;
   C f[L::Q];
   gather<L, S, G>(p, src, n, cls, f);
-  const size_t N = (size_t)p.ncell;
+  const size_t N = (size_t)p.pitch;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) Store<S>::st(dst + i * N + n.cell, f[i]);
 }
@@ -677,7 +762,7 @@ __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p,
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const size_t N = (size_t)p.ncell;
+  const size_t N = (size_t)p.pitch;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
   if (x < p.nx && y < p.ny) {
     const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
@@ -795,7 +880,7 @@ __global__ void __launch_bounds__(256) k_loss_seed(Params<typename Store<S>::C> 
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const size_t N = (size_t)p.ncell;
+  const size_t N = (size_t)p.pitch;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
   if (x < p.nx && y < p.ny) {
     const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
@@ -825,6 +910,12 @@ __global__ void __launch_bounds__(256) k_loss_seed(Params<typename Store<S>::C> 
   block_reduce_row(sv, partials + 8 * block_linear(), false);
 }
 
+}  // namespace olb
+
+#include "olb_pair.cuh"
+
+namespace olb {
+
 // ---------------------------------------------------------------------------------
 // Host launchers (dispatch run-time pattern choices to template instances).
 // ---------------------------------------------------------------------------------
@@ -841,8 +932,21 @@ struct Launch {
 
   template <int G, int SC, bool STATS>
   static cudaError_t step_t(const HostParams& h, const void* src, void* dst, double* partials) {
-    Grid g = make_grid(h.nx, h.ny, h.nz);
-    k_step<L, S, G, SC, STATS><<<g.grid, g.block, 0, h.stream>>>(
+    if constexpr (!std::is_same<S, double>::value) {
+      if (pairs_ok(h.nx)) {
+        const StepGrid g = make_step_grid(h.nx, h.ny, h.nz, true);
+        Params<float> p = params(h);
+        p.gx = g.gx;
+        p.gy = g.gy;
+        p.tile_shift = g.tile_shift;
+        p.pair_rows = g.pair_rows;
+        k_step_pair<L, S, G, SC, STATS><<<(unsigned)g.blocks(), 256, 0, h.stream>>>(
+            p, static_cast<const S*>(src), static_cast<S*>(dst), partials);
+        return cudaGetLastError();
+      }
+    }
+    const StepGrid g = make_step_grid(h.nx, h.ny, h.nz, false);
+    k_step<L, S, G, SC, STATS><<<(unsigned)g.blocks(), 256, 0, h.stream>>>(
         params(h), static_cast<const S*>(src), static_cast<S*>(dst), partials);
     return cudaGetLastError();
   }

@@ -1,0 +1,434 @@
+// olb_pair.cuh -- step kernel that updates two neighbouring cells (x0, x0 + 1)
+// per thread, for FP32 arithmetic (FP32, FP16 and BF16 storage).
+//
+// Why pairs: the update moves 2 x 19 stored values per cell against ~150 flops,
+// and on sm_103a the FP32 arithmetic, the address arithmetic and the load/store
+// instructions of one cell per thread fill the issue slots before the memory
+// system is saturated.  Two cells per thread
+//   * read and write the 9 populations with c_x = 0 as one 64-bit (FP32) or
+//     32-bit (16-bit storage) access per pair, and every own-cell store likewise;
+//   * run the collision in paired FP32 instructions (fma/add/mul .f32x2), one
+//     instruction for both cells;
+//   * share the neighbour-index arithmetic.
+// Values stored in 16 bits are (f - w) * SCALE; the collision works directly in
+// those units by writing the density as SCALE + delta_rho and the force as
+// SCALE * F, so the scale costs no instruction.
+#pragma once
+
+// Included by olb_kernels.cuh after the shared definitions (Store, Params, Nbr,
+// outside, on_edge, stats_of, block_reduce_row, lattice tables).
+
+namespace olb {
+
+// ---------------------------------------------------------------------------------
+// Paired FP32 arithmetic.
+// ---------------------------------------------------------------------------------
+struct F2 {
+  float2 v;
+  __device__ F2() {}
+  __device__ explicit F2(float s) : v(make_float2(s, s)) {}
+  __device__ F2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ explicit F2(float2 a) : v(a) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return fma2(b, F2(-1.0f), a); }
+__device__ __forceinline__ F2 neg(F2 a) { return a * F2(-1.0f); }
+
+// Storage of populations in pairs.  SCALE: stored value = (f - w) * SCALE.
+template <class S>
+struct PairStore;
+template <>
+struct PairStore<float> {
+  static constexpr float SCALE = 1.0f;
+  static constexpr int MIN_BLOCKS = OLB_PAIR_MIN_BLOCKS;
+  __device__ static float ld1(const float* p) { return *p; }
+  __device__ static F2 ld2(const float* p) { return F2(*reinterpret_cast<const float2*>(p)); }
+  __device__ static void st1(float* p, float v) { *p = v; }
+  __device__ static void st2(float* p, F2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+};
+template <>
+struct PairStore<__half> {
+  static constexpr float SCALE = Store<__half>::kScale;
+  static constexpr int MIN_BLOCKS = OLB_PAIR16_MIN_BLOCKS;
+  __device__ static float ld1(const __half* p) { return __half2float(*p); }
+  __device__ static F2 ld2(const __half* p) { return F2(__half22float2(*reinterpret_cast<const __half2*>(p))); }
+  __device__ static void st1(__half* p, float v) { *p = __float2half_rn(v); }
+  __device__ static void st2(__half* p, F2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
+};
+template <>
+struct PairStore<__nv_bfloat16> {
+  static constexpr float SCALE = 1.0f;
+  static constexpr int MIN_BLOCKS = OLB_PAIR16_MIN_BLOCKS;
+  __device__ static float ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ static F2 ld2(const __nv_bfloat16* p) {
+    return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)));
+  }
+  __device__ static void st1(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  __device__ static void st2(__nv_bfloat16* p, F2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
+  }
+};
+
+// ---------------------------------------------------------------------------------
+// Neighbourhood of a pair: x indices for offsets -1, 0, +1, +2 around x0 (wrapped)
+// and the row bases of the 3 x 3 (dy, dz) offsets.
+// ---------------------------------------------------------------------------------
+struct PairNbr {
+  int x0, y, z;
+  int xs[4];  // x0 - 1, x0, x0 + 1, x0 + 2
+  int row[3][3];
+  __device__ __forceinline__ int at(int k, int dy, int dz) const { return row[dz + 1][dy + 1] + xs[k]; }
+  __device__ __forceinline__ int cell() const { return row[1][1] + x0; }
+};
+
+template <class L>
+__device__ __forceinline__ PairNbr make_pair_nbr(const Params<float>& p, int x0, int y, int z) {
+  PairNbr n;
+  n.x0 = x0;
+  n.y = y;
+  n.z = z;
+  n.xs[0] = x0 == 0 ? p.nx - 1 : x0 - 1;
+  n.xs[1] = x0;
+  n.xs[2] = x0 + 1;
+  n.xs[3] = x0 + 2 == p.nx ? 0 : x0 + 2;
+  const int ys[3] = {y == 0 ? p.ny - 1 : y - 1, y, y == p.ny - 1 ? 0 : y + 1};
+  int zs[3] = {z, z, z};
+  if (L::DIM == 3) {
+    zs[0] = z == 0 ? p.nz - 1 : z - 1;
+    zs[2] = z == p.nz - 1 ? 0 : z + 1;
+  }
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) n.row[dz][dy] = (zs[dz] * p.ny + ys[dy]) * p.nx;
+  return n;
+}
+
+// Load the pair of values of slot `slot` at source cells (x0 + dx, x0 + 1 + dx) of
+// the row offset (dy, dz): one paired access when dx == 0.
+template <class S>
+__device__ __forceinline__ F2 ld_pair(const S* plane, const PairNbr& n, int dx, int dy, int dz) {
+  if (dx == 0) return PairStore<S>::ld2(plane + n.at(1, dy, dz));
+  return F2(PairStore<S>::ld1(plane + n.at(1 + dx, dy, dz)), PairStore<S>::ld1(plane + n.at(2 + dx, dy, dz)));
+}
+
+template <class S>
+__device__ __forceinline__ void st_pair(S* plane, const PairNbr& n, int dx, int dy, int dz, F2 v) {
+  if (dx == 0) {
+    PairStore<S>::st2(plane + n.at(1, dy, dz), v);
+  } else {
+    PairStore<S>::st1(plane + n.at(1 + dx, dy, dz), v.v.x);
+    PairStore<S>::st1(plane + n.at(2 + dx, dy, dz), v.v.y);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Collision of a pair in scaled units (values are (f - w) * SCALE).
+//   rho_s = SCALE + sum f_s,  u = (j_s + F_s/2) / rho_s,  F_s = SCALE * F,
+//   f*_s = f_s + omega (feq_s - f_s) + (1 - omega/2) Guo_s.
+// Returns rho_s and u for the wall terms and statistics.
+// ---------------------------------------------------------------------------------
+template <class L, int SCALE_NUM>
+__device__ __forceinline__ void collide_pair(const Params<float>& p, F2 gamma, F2 (&f)[L::Q], F2& drho_s,
+                                             F2 (&j_s)[3], F2& rho_s, F2 (&u)[3]) {
+  constexpr float SCALE = (float)SCALE_NUM;
+  // moments
+  F2 d = f[0];
+  F2 jj[3] = {F2(0.0f), F2(0.0f), F2(0.0f)};
+#pragma unroll
+  for (int k = 1; k <= L::HALF; ++k) {
+    const int kp = k + L::HALF;
+    d = d + f[k] + f[kp];
+    const F2 a = f[kp] - f[k];
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      if (L::c(kp, dd) == 1) jj[dd] = jj[dd] + a;
+      if (L::c(kp, dd) == -1) jj[dd] = jj[dd] - a;
+    }
+  }
+  drho_s = d;
+  j_s[0] = jj[0];
+  j_s[1] = jj[1];
+  j_s[2] = jj[2];
+  const F2 rho = d + F2(SCALE);
+  const F2 inv = F2(__frcp_rn(rho.v.x), __frcp_rn(rho.v.y));
+  rho_s = rho;
+  F2 up[3];
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    u[dd] = (jj[dd] + F2(p.half_force[dd] * SCALE)) * inv;
+    up[dd] = gamma * u[dd];
+  }
+  F2 usq = up[0] * up[0];
+  usq = fma2(up[1], up[1], usq);
+  if (L::DIM == 3) usq = fma2(up[2], up[2], usq);
+  const float om = p.omega;
+  const F2 one_m_om(1.0f - om);
+  const F2 omv(om);
+  // A = drho_s - 1.5 rho_s usq ; B = 4.5 rho_s ; T = 3 rho_s
+  const F2 A = fma2(F2(-1.5f) * rho, usq, d);
+  const F2 B = F2(4.5f) * rho;
+  const F2 T = F2(3.0f) * rho;
+  const float gf = 1.0f - 0.5f * om;
+  F2 uF(0.0f);
+  if (p.forced) {
+    uF = up[0] * F2(p.force[0] * SCALE);
+    uF = fma2(up[1], F2(p.force[1] * SCALE), uF);
+    uF = fma2(up[2], F2(p.force[2] * SCALE), uF);
+  }
+  {
+    const float w0 = (float)L::w(0);
+    const F2 feq = F2(w0) * A;
+    F2 v = fma2(one_m_om, f[0], omv * feq);
+    if (p.forced) v = fma2(F2(-3.0f * gf * w0), uF, v);
+    f[0] = v;
+  }
+#pragma unroll
+  for (int k = 1; k <= L::HALF; ++k) {
+    const int kp = k + L::HALF;
+    const float wk = (float)L::w(k);
+    F2 cu(0.0f);
+    float cFs = 0.0f;
+    bool first = true;
+#pragma unroll
+    for (int dd = 0; dd < L::DIM; ++dd) {
+      const int c = L::c(kp, dd);
+      if (c != 0) {
+        if (first) {
+          cu = c > 0 ? up[dd] : neg(up[dd]);
+          first = false;
+        } else {
+          cu = c > 0 ? cu + up[dd] : cu - up[dd];
+        }
+        cFs += c * p.force[dd] * SCALE;
+      }
+    }
+    const F2 sym = F2(wk) * fma2(B, cu * cu, A);
+    const F2 anti = F2(wk) * T * cu;
+    F2 fp = fma2(one_m_om, f[kp], omv * (sym + anti));
+    F2 fm = fma2(one_m_om, f[k], omv * (sym - anti));
+    if (p.forced) {
+      // Guo: gf w (9 cu cF - 3 u'.F) +- 3 gf w cF   (F in scaled units)
+      const F2 gs = fma2(F2(9.0f * gf * wk * cFs), cu, F2(-3.0f * gf * wk) * uF);
+      const float ga = 3.0f * gf * wk * cFs;
+      fp = fp + gs + F2(ga);
+      fm = fm + gs - F2(ga);
+    }
+    f[kp] = fp;
+    f[k] = fm;
+  }
+}
+
+// 6 w_i (c_i . u_w) of wall material m (FP32).
+template <class L>
+__device__ __forceinline__ float wall_term_f(const Params<float>& p, int i, int m) {
+  const double* uw = p.wall_u + 4 * m;
+  return (float)(6.0 * L::w(i) * (L::c(i, 0) * uw[0] + L::c(i, 1) * uw[1] + L::c(i, 2) * uw[2]));
+}
+
+// ---------------------------------------------------------------------------------
+// The paired step kernel (patterns as in k_step, see scatter for the bounce-back
+// storage rules).  Requires nx even; tiles of (2 << tile_shift) cells along x by
+// (256 >> tile_shift) rows.
+// ---------------------------------------------------------------------------------
+template <class L, class S, int G, int SC, bool STATS>
+__global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Params<float> p, const S* src, S* dst,
+                                                                       double* partials) {
+  constexpr int SC_NUM = (int)PairStore<S>::SCALE;
+  constexpr float INV_SCALE = 1.0f / PairStore<S>::SCALE;
+  float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int tid = threadIdx.x;
+  int x0, y, z;
+  bool active;
+  if (p.pair_rows > 0) {
+    // Row-group mapping: the block updates pair_rows whole rows of P = nx/2 pairs.
+    // Threads [0, R (P-2)) take the inner pairs 1 .. P-2 row by row; the last 2R
+    // threads take the first and last pair of each row -- the ones next to walls
+    // on the x faces -- so that only the block's last warp runs their code.
+    const int P = p.nx >> 1, R = p.pair_rows;
+    const int inner = P - 2;
+    int r, q;
+    if (tid < R * inner) {
+      r = tid / inner;
+      q = 1 + (tid - r * inner);
+    } else {
+      const int e = tid - R * inner;
+      r = e >> 1;
+      q = (e & 1) ? P - 1 : 0;
+    }
+    const int row = blockIdx.x * R + r;
+    active = tid < R * P && row < p.ny * p.nz;
+    y = row % p.ny;
+    z = row / p.ny;
+    x0 = 2 * q;
+  } else {
+    const int t = blockIdx.x;
+    const int tz = t / p.gx;
+    const int bx = t - tz * p.gx;
+    const int by = tz % p.gy;
+    z = tz / p.gy;
+    x0 = 2 * ((bx << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1)));
+    y = by * (256 >> p.tile_shift) + (tid >> p.tile_shift);
+    active = x0 < p.nx && y < p.ny;
+  }
+  if (active) {
+    const PairNbr n = make_pair_nbr<L>(p, x0, y, z);
+    const int cell = n.cell();
+    const size_t N = (size_t)p.pitch;
+    uint32_t w[2] = {kWordFluid, kWordFluid};
+    if (!p.all_fluid) {
+      const uint2 ww = *reinterpret_cast<const uint2*>(p.word + cell);
+      w[0] = ww.x;
+      w[1] = ww.y;
+    }
+    F2 f[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const int slot = (G == G_OWN || G == G_PULL) ? i : opp<L>(i);
+      if (G == G_OWN)
+        f[i] = PairStore<S>::ld2(src + i * N + cell);
+      else
+        f[i] = ld_pair(src + slot * N, n, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+    }
+    F2 gamma(1.0f);
+    if (p.gamma) gamma = F2(*reinterpret_cast<const float2*>(p.gamma + cell));
+    // links leaving the domain (no cell holds their bounce-back value)
+    bool edge[2] = {false, false};
+    if (G != G_OWN && p.outside_links) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        Nbr c1;
+        c1.x = x0 + h;
+        c1.y = y;
+        c1.z = z;
+        edge[h] = on_edge<L>(p, x0 + h, y, z);
+        if (edge[h]) {
+#pragma unroll
+          for (int i = 1; i < L::Q; ++i) {
+            if (outside(p, c1, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2))) {
+              const int own = (G == G_PULL) ? opp<L>(i) : i;
+              const float v = PairStore<S>::ld1(src + own * N + cell + h);
+              if (h == 0) f[i].v.x = v; else f[i].v.y = v;
+            }
+          }
+        }
+      }
+    }
+    F2 drho, j[3], rho, u[3];
+    collide_pair<L, SC_NUM>(p, gamma, f, drho, j, rho, u);
+    const bool fl0 = (w[0] & kWordFluid) != 0, fl1 = (w[1] & kWordFluid) != 0;
+    if (SC == S_OWN || SC == S_OWN_SWAP) {
+      // own slots: one paired store per population when both cells are fluid
+      if (fl0 && fl1) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) PairStore<S>::st2(dst + ((SC == S_OWN) ? i : opp<L>(i)) * N + cell, f[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          S* q = dst + ((SC == S_OWN) ? i : opp<L>(i)) * N + cell;
+          if (fl0) PairStore<S>::st1(q, f[i].v.x);
+          if (fl1) PairStore<S>::st1(q + 1, f[i].v.y);
+        }
+      }
+      // bounce-back links: the bounced population goes into the wall cell x + c_i,
+      // in the slot that x reads there at the next step
+      const uint32_t l0 = fl0 ? (w[0] & kWordLinks) : 0u;
+      const uint32_t l1 = fl1 ? (w[1] & kWordLinks) : 0u;
+      if (l0 | l1) {
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+          const int slot = (SC == S_OWN) ? opp<L>(i) : i;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if ((h == 0 ? l0 : l1) & (1u << i)) {
+              const int tx = 1 + h + L::c(i, 0);  // index into xs of x + c_i
+              float v = h == 0 ? f[i].v.x : f[i].v.y;
+              if (w[h] & kWordMoving) {
+                const int wm = p.mat[n.at(tx, L::c(i, 1), L::c(i, 2))];
+                if (wm >= 3) v -= (h == 0 ? rho.v.x : rho.v.y) * wall_term_f<L>(p, i, wm);  // rho_s 6 w c.u_w
+              }
+              PairStore<S>::st1(dst + slot * N + n.at(tx, L::c(i, 1), L::c(i, 2)), v);
+            }
+          }
+        }
+      }
+      if (OLB_SOLID_FILL) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!(h == 0 ? fl0 : fl1)) {
+            const uint32_t nb = w[h] & kWordLinks;
+#pragma unroll
+            for (int k = 0; k < L::Q; ++k) {
+              const int b = (SC == S_OWN) ? k : opp<L>(k);
+              if (k == 0 || !(nb & (1u << b))) PairStore<S>::st1(dst + k * N + cell + h, 0.0f);
+            }
+          }
+        }
+      }
+    } else {  // S_PUSH
+      const bool plain = fl0 && fl1 && !((w[0] | w[1]) & (kWordLinks | kWordMoving)) && !edge[0] && !edge[1];
+      if (plain) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) st_pair(dst + i * N, n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
+      } else {
+        // per cell, with bounce-back links, domain edges and non-fluid cells
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t wd = w[h];
+          const int c = cell + h;
+          const float rh = h == 0 ? rho.v.x : rho.v.y;
+          Nbr c1;
+          c1.x = x0 + h;
+          c1.y = y;
+          c1.z = z;
+          if (wd & kWordFluid) {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+              const float fi = h == 0 ? f[i].v.x : f[i].v.y;
+              const int tx = 1 + h + L::c(i, 0);
+              const bool wall = i != 0 && (wd & (1u << i));
+              const bool out = i != 0 && edge[h] && outside(p, c1, L::c(i, 0), L::c(i, 1), L::c(i, 2));
+              if (wall || out) {
+                float bounced = fi;
+                if (wall && (wd & kWordMoving)) {
+                  const int wm = p.mat[n.at(tx, L::c(i, 1), L::c(i, 2))];
+                  if (wm >= 3) bounced -= rh * wall_term_f<L>(p, i, wm);
+                }
+                PairStore<S>::st1(dst + opp<L>(i) * N + c, bounced);
+              } else {
+                PairStore<S>::st1(dst + i * N + n.at(tx, L::c(i, 1), L::c(i, 2)), fi);
+              }
+            }
+          } else if (OLB_SOLID_FILL) {
+            const uint32_t nb = wd & kWordLinks;
+#pragma unroll
+            for (int k = 0; k < L::Q; ++k)
+              if (k == 0 || !(nb & (1u << opp<L>(k)))) PairStore<S>::st1(dst + k * N + c, 0.0f);
+          }
+        }
+      }
+    }
+    if (STATS) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (w[h] & kWordFluid) {
+          const float dr = (h == 0 ? drho.v.x : drho.v.y) * INV_SCALE;
+          float jv[3], uv[3], v[8];
+#pragma unroll
+          for (int dd = 0; dd < 3; ++dd) {
+            jv[dd] = (h == 0 ? j[dd].v.x : j[dd].v.y) * INV_SCALE;
+            uv[dd] = h == 0 ? u[dd].v.x : u[dd].v.y;
+          }
+          stats_of(dr, jv, uv, v);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) sv[k] = (k == 5) ? fmaxf(sv[k], v[k]) : sv[k] + v[k];
+        }
+      }
+    }
+  }
+  if (STATS) block_reduce_row(sv, partials + 8 * (int64_t)blockIdx.x, false);
+}
+
+}  // namespace olb

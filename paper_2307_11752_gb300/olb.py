@@ -56,6 +56,7 @@ SIGNATURES = {
     "olb_synchronize": [_P],
     "olb_counters": [_P, _P, _P],
     "olb_last_error": [],
+    "olb_build_info": [],
 }
 
 
@@ -85,9 +86,13 @@ def load(path: str = LIB_PATH):
     for name, args in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "olb_last_error" else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name in ("olb_last_error", "olb_build_info") else ctypes.c_int
     _lib = lib
     return lib
+
+
+def build_info() -> str:
+    return load().olb_build_info().decode()
 
 
 def _call(name: str, *args) -> int:
