@@ -202,6 +202,32 @@ int olb_synchronize(olb_handle h);
  * olb_set_populations) and the number of kernels the handle has launched. */
 int olb_counters(olb_handle h, int64_t* time, int64_t* kernel_launches);
 
+/* Lattice statistics (the 7 values of olb_diagnostics) of a canonical population
+ * array, for callers that cannot allocate device memory: a process whose device
+ * memory is already reserved by another allocator (such as a framework's caching
+ * allocator), or a caller that cannot accept the device-wide synchronisation of
+ * cudaMalloc/cudaFree.  This entry point allocates nothing: its per-block partial
+ * sums live in a fixed array in the library's own device memory (4 MiB, held on
+ * every GPU that loads the library until the process exits).  There is no
+ * counterpart in the OpenLB guide; it is an interface of this library.
+ *   f        device double [q][cells], canonical populations (as olb_get_populations)
+ *   material device uint8 [cells] (1 = fluid; only fluid cells count) or NULL (all fluid)
+ *   force    host double[3] used in u = (j + F/2)/rho, or NULL (no force)
+ *   out      device double[7]: sum rho, sum j (3), sum |u|^2/2, max |u|, non-finite cells
+ *   stream   cudaStream_t the work is queued on (asynchronous: out is ready when the
+ *            stream reaches this point; non-finite cells are reported in out[6] only)
+ * The first call on a device looks up the device address of the fixed array (with
+ * that device current); make that first call before any stream capture.  All calls
+ * on a device share the array, so calls that overlap on the GPU (on different
+ * streams) race; order them on one stream.  Each call overwrites every partial sum
+ * it reads, so no clearing is needed between calls.
+ * Errors: OLB_ERR_ARG for more than 16,777,216 cells (65,536 blocks of 256 cells,
+ * the capacity of the fixed array), a bad descriptor or size, null f/out, or
+ * arrays that are not device memory; OLB_ERR_CUDA for a failed launch. */
+int olb_statistics_noalloc(olb_descriptor d, int nx, int ny, int nz, const double* f,
+                           const uint8_t* material, const double* force, double* out,
+                           void* cuda_stream);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* olb_last_error(void);
 

@@ -206,6 +206,11 @@ void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, u
 
 }  // namespace
 
+int olb::set_error(int code, const char* msg) {
+  g_err = msg ? msg : "";
+  return code;
+}
+
 // ---------------------------------------------------------------------------------
 // Handle
 // ---------------------------------------------------------------------------------

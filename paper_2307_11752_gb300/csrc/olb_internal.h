@@ -99,6 +99,9 @@ const KernelTable* table_d3q19_f32();
 const KernelTable* table_d3q19_f16();
 const KernelTable* table_d3q19_bf16();
 
+// Record the message returned by olb_last_error() on this thread; returns code.
+int set_error(int code, const char* msg);
+
 // Sum the first `rows` rows of 8 doubles into out[8] (deterministic order).
 cudaError_t reduce_partials(const double* partials, int64_t rows, double* out, cudaStream_t s);
 

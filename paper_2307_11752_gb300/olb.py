@@ -55,6 +55,7 @@ SIGNATURES = {
     "olb_adjoint_run": [_P, _I64, _I64, _P, _P, _P, _P],
     "olb_synchronize": [_P],
     "olb_counters": [_P, _P, _P],
+    "olb_statistics_noalloc": [_I, _I, _I, _I, _P, _P, _P, _P, _P],
     "olb_last_error": [],
     "olb_build_info": [],
 }

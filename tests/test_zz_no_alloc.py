@@ -1,0 +1,90 @@
+"""olb_statistics_noalloc: the statistics reduction for callers that cannot
+allocate device memory (their GPU memory is held by another allocator, or they
+cannot accept cudaMalloc's device-wide synchronisation).  It keeps its partial
+sums in a fixed array inside the library instead of allocating.
+
+Checked through the C ABI against the existing entry point olb_diagnostics on
+the same lattice state, on two calls in a row (the second on a later state, so
+a stale partial sum left by the first call would show), within the FP64
+tolerances of the other statistics tests.  This file is collected last so that
+a run stopping at its first failure has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2307_11752_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def olb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_11752_gb300 import build, olb as _olb
+    build.build()
+    _olb.load()
+    return _olb
+
+
+def _noalloc(olb, lat, f, material, force, stream):
+    import torch
+
+    out = torch.full((7,), float("nan"), dtype=torch.float64, device="cuda")
+    F = (ctypes.c_double * 3)(*force)
+    rc = olb.load().olb_statistics_noalloc(lat.descriptor, lat.nx, lat.ny, lat.nz, f.data_ptr(),
+                                           material.data_ptr(), F, out.data_ptr(),
+                                           ctypes.c_void_p(stream.cuda_stream))
+    assert rc == 0, olb.load().olb_last_error().decode()
+    stream.synchronize()
+    return out.cpu().numpy()
+
+
+def _agree(a, b):
+    assert abs(a[0] - b[0]) <= 1e-12 * abs(b[0])                      # mass
+    assert np.allclose(a[1:4], b[1:4], rtol=1e-9, atol=1e-15)         # momentum
+    assert abs(a[4] - b[4]) <= 1e-10 * abs(b[4])                      # energy
+    assert abs(a[5] - b[5]) <= 1e-12 * abs(b[5])                      # max |u|
+    assert a[6] == b[6] == 0
+
+
+@pytest.mark.parametrize("d,shape", [(1, (30, 22, 17)), (0, (45, 33, 1))])
+def test_noalloc_statistics_match_diagnostics_twice(olb, d, shape):
+    import torch
+
+    nx, ny, nz = shape
+    m = I.cavity_box(nx, ny, nz)
+    force = (2e-6, -1e-6, 0.0)
+    lat = olb.Lattice(d, shape, dtype="f64", scheme="pull")
+    lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 0)
+    lat.set_wall_velocity(I.LID, (0.05, 0.0, 0.0))
+    lat.set_bgk(0.6)
+    lat.set_force(force)
+    lat.init_equilibrium()
+    mat = torch.from_numpy(m.reshape(-1).copy()).cuda()
+    stream = torch.cuda.current_stream()
+    for steps in (25, 40):  # two calls in a row, on different states
+        lat.step(steps)
+        f = lat.get_populations()
+        got = _noalloc(olb, lat, f, mat, force, stream)
+        _agree(got, lat.diagnostics())
+    lat.close()
+
+
+def test_noalloc_rejects_lattices_beyond_its_fixed_array(olb):
+    import torch
+
+    dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
+    out = torch.zeros(7, dtype=torch.float64, device="cuda")
+    lib = olb.load()
+    rc = lib.olb_statistics_noalloc(1, 257, 256, 256, dummy.data_ptr(), None, None, out.data_ptr(), None)
+    assert rc == -1
+    assert "16,777,216" in lib.olb_last_error().decode()
+    # host memory is refused rather than staged (staging would allocate)
+    host = np.zeros(19 * 8, dtype=np.float64)
+    rc = lib.olb_statistics_noalloc(1, 2, 2, 2, host.ctypes.data, None, None, out.data_ptr(), None)
+    assert rc == -1
