@@ -130,7 +130,7 @@ def measured_peak_gbs():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for rel in ("paper_2307_11752_gb300/csrc/olb_kernels.cuh",):
+    for rel in ("paper_2307_11752_gb300/csrc/olb_kernels.cuh", "paper_2307_11752_gb300/csrc/olb_pair.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -343,7 +343,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": cfg,
-        "roofline": {"bound": "hbm", "kernel": "k_step<D3Q19,float,pull>", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_step_pair<D3Q19,float,G_PULL,S_OWN>", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "traffic": None if traffic is None else round(traffic),
@@ -352,6 +352,7 @@ def run_ours(args):
         "e2e": {"value": round(e2e_units / e2e_sec / 1e6, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        "build": olb.build_info(),
         "clocks": clocks,
         "statistics_last_step": {"mass": stats[0], "max_u": stats[5], "nonfinite": stats[6]},
     }
