@@ -461,7 +461,7 @@ const char* olb_last_error(void) { return g_err.c_str(); }
 #define OLB_STR(x) OLB_STR2(x)
 const char* olb_build_info(void) {
   return "sm_103a step_min_blocks=" OLB_STR(OLB_STEP_MIN_BLOCKS) " pair_min_blocks=" OLB_STR(OLB_PAIR_MIN_BLOCKS) " pair16_min_blocks=" OLB_STR(OLB_PAIR16_MIN_BLOCKS)
-         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " row_groups=" OLB_STR(OLB_ROW_GROUPS) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
+         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " row_groups=" OLB_STR(OLB_ROW_GROUPS) " xwall_pairs=" OLB_STR(OLB_XWALL_PAIRS) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
 #ifdef OLB_NO_PAIRS
          " pairs=off"
 #else

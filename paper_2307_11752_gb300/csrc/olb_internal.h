@@ -59,6 +59,7 @@ struct StepGrid {
   int pair_rows = 0;    // paired kernel: rows per block (row-group mapping), 0 = tiles
   int64_t row_blocks = 0;
   int64_t blocks() const { return pair_rows > 0 ? row_blocks : (int64_t)gx * gy * nz; }
+  dim3 dims() const { return pair_rows > 0 ? dim3((unsigned)row_blocks, 1, 1) : dim3(gx, gy, nz); }
 };
 StepGrid make_step_grid(int nx, int ny, int nz, bool pairs);
 // The paired kernel runs for FP32-arithmetic storage types when nx is even.

@@ -558,13 +558,9 @@ __global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typena
   using C = typename Store<S>::C;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
   const int tid = threadIdx.x;
-  const int t = blockIdx.x;
-  const int tz = t / p.gx;
-  const int bx = t - tz * p.gx;
-  const int by = tz % p.gy;
-  const int z = tz / p.gy;
-  const int x = (bx << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1));
-  const int y = by * (256 >> p.tile_shift) + (tid >> p.tile_shift);
+  const int z = blockIdx.z;
+  const int x = (blockIdx.x << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1));
+  const int y = blockIdx.y * (256 >> p.tile_shift) + (tid >> p.tile_shift);
   if (x < p.nx && y < p.ny) {
     const Nbr n = make_nbr<L>(p, x, y, z);
     const uint32_t w = p.all_fluid ? kWordFluid : p.word[n.cell];
@@ -585,7 +581,7 @@ __global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typena
       solid_fill<L, S, SC>(p, dst, n, w & kWordLinks);
     }
   }
-  if (STATS) block_reduce_row(sv, partials + 8 * (int64_t)blockIdx.x, false);
+  if (STATS) block_reduce_row(sv, partials + 8 * block_linear(), false);
 }
 
 // Canonical f(t) = f_shifted + w in double ([q][cells]); non-fluid cells 0.
@@ -940,13 +936,21 @@ struct Launch {
         p.gy = g.gy;
         p.tile_shift = g.tile_shift;
         p.pair_rows = g.pair_rows;
-        k_step_pair<L, S, G, SC, STATS><<<(unsigned)g.blocks(), 256, 0, h.stream>>>(
-            p, static_cast<const S*>(src), static_cast<S*>(dst), partials);
+        Planes<S> pl;
+        for (int i = 0; i < 19; ++i) {
+          const int k = i < L::Q ? i : 0;
+          pl.src[i] = static_cast<const S*>(src) + (size_t)k * h.pitch;
+          pl.dst[i] = static_cast<S*>(dst) + (size_t)k * h.pitch;
+        }
+        if (h.cls == nullptr)  // all fluid, all periodic
+          k_step_pair<L, S, G, SC, STATS, false><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
+        else
+          k_step_pair<L, S, G, SC, STATS, true><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
         return cudaGetLastError();
       }
     }
     const StepGrid g = make_step_grid(h.nx, h.ny, h.nz, false);
-    k_step<L, S, G, SC, STATS><<<(unsigned)g.blocks(), 256, 0, h.stream>>>(
+    k_step<L, S, G, SC, STATS><<<g.dims(), 256, 0, h.stream>>>(
         params(h), static_cast<const S*>(src), static_cast<S*>(dst), partials);
     return cudaGetLastError();
   }

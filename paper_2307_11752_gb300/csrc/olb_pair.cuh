@@ -71,6 +71,16 @@ struct PairStore<__nv_bfloat16> {
   }
 };
 
+// Base pointers of the population planes of the source and destination buffers,
+// passed as kernel parameters: each access is then one index add and one wide
+// multiply-add on a constant-bank operand, instead of recomputing
+// buffer + slot * pitch per access.
+template <class S>
+struct Planes {
+  const S* src[19];
+  S* dst[19];
+};
+
 // ---------------------------------------------------------------------------------
 // Neighbourhood of a pair: x indices for offsets -1, 0, +1, +2 around x0 (wrapped)
 // and the row bases of the 3 x 3 (dy, dz) offsets.
@@ -228,14 +238,53 @@ __device__ __forceinline__ float wall_term_f(const Params<float>& p, int i, int 
   return (float)(6.0 * L::w(i) * (L::c(i, 0) * uw[0] + L::c(i, 1) * uw[1] + L::c(i, 2) * uw[2]));
 }
 
+// Special store paths for pairs at walls on the x faces (see the store phase).
+#ifndef OLB_XWALL_PAIRS
+#define OLB_XWALL_PAIRS 1
+#endif
+
+// Link bits of the directions with c_x == cx (all non-rest directions for cx == 0
+// is not used; see ghost_stores).
+template <class L>
+__host__ __device__ constexpr uint32_t dir_mask(int cx) {
+  uint32_t m = 0;
+  for (int i = 1; i < L::Q; ++i)
+    if (L::c(i, 0) == cx) m |= 1u << i;
+  return m;
+}
+
+// Bounce-back stores of cell h of a pair for the links set in `l`, testing only
+// the directions with c_x == CX (CX == 0: all directions).
+template <class L, class S, int SC, int CX>
+__device__ __forceinline__ void ghost_stores(const Params<float>& p, const Planes<S>& pl, const PairNbr& n, int h,
+                                             uint32_t l, uint32_t word, const F2 (&f)[L::Q], F2 rho) {
+#pragma unroll
+  for (int i = 1; i < L::Q; ++i) {
+    if (CX != 0 && L::c(i, 0) != CX) continue;
+    if (l & (1u << i)) {
+      const int tx = 1 + h + L::c(i, 0);  // index into xs of x + c_i
+      float v = h == 0 ? f[i].v.x : f[i].v.y;
+      if (word & kWordMoving) {
+        const int wm = p.mat[n.at(tx, L::c(i, 1), L::c(i, 2))];
+        if (wm >= 3) v -= (h == 0 ? rho.v.x : rho.v.y) * wall_term_f<L>(p, i, wm);  // rho_s 6 w c.u_w
+      }
+      const int slot = (SC == S_OWN) ? opp<L>(i) : i;
+      PairStore<S>::st1(pl.dst[slot] + n.at(tx, L::c(i, 1), L::c(i, 2)), v);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // The paired step kernel (patterns as in k_step, see scatter for the bounce-back
 // storage rules).  Requires nx even; tiles of (2 << tile_shift) cells along x by
-// (256 >> tile_shift) rows.
+// (256 >> tile_shift) rows.  WALLS = false is the instance for lattices whose cells
+// are all fluid with every axis periodic: it carries no boundary code at all, so
+// the boundary paths cannot cost registers or scheduling freedom there.
 // ---------------------------------------------------------------------------------
-template <class L, class S, int G, int SC, bool STATS>
-__global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Params<float> p, const S* src, S* dst,
-                                                                       double* partials) {
+template <class L, class S, int G, int SC, bool STATS, bool WALLS>
+__global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Params<float> p,
+                                                                             const __grid_constant__ Planes<S> pl,
+                                                                             double* partials) {
   constexpr int SC_NUM = (int)PairStore<S>::SCALE;
   constexpr float INV_SCALE = 1.0f / PairStore<S>::SCALE;
   float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -258,27 +307,22 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
       r = e >> 1;
       q = (e & 1) ? P - 1 : 0;
     }
-    const int row = blockIdx.x * R + r;
+    const int row = (int)block_linear() * R + r;
     active = tid < R * P && row < p.ny * p.nz;
     y = row % p.ny;
     z = row / p.ny;
     x0 = 2 * q;
   } else {
-    const int t = blockIdx.x;
-    const int tz = t / p.gx;
-    const int bx = t - tz * p.gx;
-    const int by = tz % p.gy;
-    z = tz / p.gy;
-    x0 = 2 * ((bx << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1)));
-    y = by * (256 >> p.tile_shift) + (tid >> p.tile_shift);
+    z = blockIdx.z;
+    x0 = 2 * ((blockIdx.x << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1)));
+    y = blockIdx.y * (256 >> p.tile_shift) + (tid >> p.tile_shift);
     active = x0 < p.nx && y < p.ny;
   }
   if (active) {
     const PairNbr n = make_pair_nbr<L>(p, x0, y, z);
     const int cell = n.cell();
-    const size_t N = (size_t)p.pitch;
     uint32_t w[2] = {kWordFluid, kWordFluid};
-    if (!p.all_fluid) {
+    if (WALLS) {
       const uint2 ww = *reinterpret_cast<const uint2*>(p.word + cell);
       w[0] = ww.x;
       w[1] = ww.y;
@@ -288,15 +332,15 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
     for (int i = 0; i < L::Q; ++i) {
       const int slot = (G == G_OWN || G == G_PULL) ? i : opp<L>(i);
       if (G == G_OWN)
-        f[i] = PairStore<S>::ld2(src + i * N + cell);
+        f[i] = PairStore<S>::ld2(pl.src[i] + cell);
       else
-        f[i] = ld_pair(src + slot * N, n, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+        f[i] = ld_pair(pl.src[slot], n, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
     }
     F2 gamma(1.0f);
     if (p.gamma) gamma = F2(*reinterpret_cast<const float2*>(p.gamma + cell));
     // links leaving the domain (no cell holds their bounce-back value)
     bool edge[2] = {false, false};
-    if (G != G_OWN && p.outside_links) {
+    if (WALLS && G != G_OWN && p.outside_links) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         Nbr c1;
@@ -309,7 +353,7 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
           for (int i = 1; i < L::Q; ++i) {
             if (outside(p, c1, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2))) {
               const int own = (G == G_PULL) ? opp<L>(i) : i;
-              const float v = PairStore<S>::ld1(src + own * N + cell + h);
+              const float v = PairStore<S>::ld1(pl.src[own] + cell + h);
               if (h == 0) f[i].v.x = v; else f[i].v.y = v;
             }
           }
@@ -319,38 +363,62 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
     F2 drho, j[3], rho, u[3];
     collide_pair<L, SC_NUM>(p, gamma, f, drho, j, rho, u);
     const bool fl0 = (w[0] & kWordFluid) != 0, fl1 = (w[1] & kWordFluid) != 0;
-    if (SC == S_OWN || SC == S_OWN_SWAP) {
-      // own slots: one paired store per population when both cells are fluid
-      if (fl0 && fl1) {
+    if (!WALLS) {
+      // every cell fluid, every axis periodic: plain paired stores only
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) PairStore<S>::st2(dst + ((SC == S_OWN) ? i : opp<L>(i)) * N + cell, f[i]);
+      for (int i = 0; i < L::Q; ++i) {
+        if (SC == S_PUSH)
+          st_pair(pl.dst[i], n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
+        else
+          PairStore<S>::st2(pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell, f[i]);
+      }
+    } else if (SC == S_OWN || SC == S_OWN_SWAP) {
+      // Own slots, one paired store per population.  A non-fluid cell's slots hold
+      // nothing except its bounce-back slots (written by fluid neighbours, bits nb):
+      // a pair whose non-fluid cell has bounce-back slots only on the side of its
+      // fluid partner (the usual case at a wall on an x face) still stores in pairs,
+      // except for the 5 directions that point from the non-fluid cell into its
+      // partner, which store the fluid cell alone.
+      const uint32_t nb0 = w[0] & kWordLinks, nb1 = w[1] & kWordLinks;
+      const bool lo = OLB_XWALL_PAIRS && !fl0 && fl1 && !(nb0 & ~dir_mask<L>(1));   // non-fluid x0, fluid x0 + 1
+      const bool hi = OLB_XWALL_PAIRS && fl0 && !fl1 && !(nb1 & ~dir_mask<L>(-1));  // fluid x0, non-fluid x0 + 1
+      if ((fl0 && fl1) || lo || hi) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          S* q = pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell;
+          if (L::c(i, 0) == 1 && lo) {
+            PairStore<S>::st1(q + 1, f[i].v.y);
+          } else if (L::c(i, 0) == -1 && hi) {
+            PairStore<S>::st1(q, f[i].v.x);
+          } else {
+            PairStore<S>::st2(q, f[i]);
+          }
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-          S* q = dst + ((SC == S_OWN) ? i : opp<L>(i)) * N + cell;
+          S* q = pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell;
           if (fl0) PairStore<S>::st1(q, f[i].v.x);
           if (fl1) PairStore<S>::st1(q + 1, f[i].v.y);
         }
       }
-      // bounce-back links: the bounced population goes into the wall cell x + c_i,
-      // in the slot that x reads there at the next step
-      const uint32_t l0 = fl0 ? (w[0] & kWordLinks) : 0u;
-      const uint32_t l1 = fl1 ? (w[1] & kWordLinks) : 0u;
+      // Bounce-back links: the bounced population goes into the wall cell x + c_i,
+      // in the slot that x reads there at the next step.  A cell next to a wall on
+      // an x face has its links only among the 5 directions with c_x = -1 (or +1);
+      // it tests only those.
+      const uint32_t l0 = fl0 ? nb0 : 0u;
+      const uint32_t l1 = fl1 ? nb1 : 0u;
       if (l0 | l1) {
 #pragma unroll
-        for (int i = 1; i < L::Q; ++i) {
-          const int slot = (SC == S_OWN) ? opp<L>(i) : i;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if ((h == 0 ? l0 : l1) & (1u << i)) {
-              const int tx = 1 + h + L::c(i, 0);  // index into xs of x + c_i
-              float v = h == 0 ? f[i].v.x : f[i].v.y;
-              if (w[h] & kWordMoving) {
-                const int wm = p.mat[n.at(tx, L::c(i, 1), L::c(i, 2))];
-                if (wm >= 3) v -= (h == 0 ? rho.v.x : rho.v.y) * wall_term_f<L>(p, i, wm);  // rho_s 6 w c.u_w
-              }
-              PairStore<S>::st1(dst + slot * N + n.at(tx, L::c(i, 1), L::c(i, 2)), v);
-            }
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t l = h == 0 ? l0 : l1;
+          if (l) {
+            if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(-1)))
+              ghost_stores<L, S, SC, -1>(p, pl, n, h, l, w[h], f, rho);
+            else if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(1)))
+              ghost_stores<L, S, SC, 1>(p, pl, n, h, l, w[h], f, rho);
+            else
+              ghost_stores<L, S, SC, 0>(p, pl, n, h, l, w[h], f, rho);
           }
         }
       }
@@ -362,7 +430,7 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
 #pragma unroll
             for (int k = 0; k < L::Q; ++k) {
               const int b = (SC == S_OWN) ? k : opp<L>(k);
-              if (k == 0 || !(nb & (1u << b))) PairStore<S>::st1(dst + k * N + cell + h, 0.0f);
+              if (k == 0 || !(nb & (1u << b))) PairStore<S>::st1(pl.dst[k] + cell + h, 0.0f);
             }
           }
         }
@@ -371,7 +439,7 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
       const bool plain = fl0 && fl1 && !((w[0] | w[1]) & (kWordLinks | kWordMoving)) && !edge[0] && !edge[1];
       if (plain) {
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) st_pair(dst + i * N, n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
+        for (int i = 0; i < L::Q; ++i) st_pair(pl.dst[i], n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
       } else {
         // per cell, with bounce-back links, domain edges and non-fluid cells
 #pragma unroll
@@ -396,16 +464,16 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
                   const int wm = p.mat[n.at(tx, L::c(i, 1), L::c(i, 2))];
                   if (wm >= 3) bounced -= rh * wall_term_f<L>(p, i, wm);
                 }
-                PairStore<S>::st1(dst + opp<L>(i) * N + c, bounced);
+                PairStore<S>::st1(pl.dst[opp<L>(i)] + c, bounced);
               } else {
-                PairStore<S>::st1(dst + i * N + n.at(tx, L::c(i, 1), L::c(i, 2)), fi);
+                PairStore<S>::st1(pl.dst[i] + n.at(tx, L::c(i, 1), L::c(i, 2)), fi);
               }
             }
           } else if (OLB_SOLID_FILL) {
             const uint32_t nb = wd & kWordLinks;
 #pragma unroll
             for (int k = 0; k < L::Q; ++k)
-              if (k == 0 || !(nb & (1u << opp<L>(k)))) PairStore<S>::st1(dst + k * N + c, 0.0f);
+              if (k == 0 || !(nb & (1u << opp<L>(k)))) PairStore<S>::st1(pl.dst[k] + c, 0.0f);
           }
         }
       }
@@ -428,7 +496,7 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
       }
     }
   }
-  if (STATS) block_reduce_row(sv, partials + 8 * (int64_t)blockIdx.x, false);
+  if (STATS) block_reduce_row(sv, partials + 8 * block_linear(), false);
 }
 
 }  // namespace olb
