@@ -267,21 +267,15 @@ def variants(olb, torch):
             "roofline_frac": round(n ** 3 * b / (ms * 1e-3) / 1e9 / peak, 4)}
         lat.close()
         torch.cuda.empty_cache()
-    # adjoint, porous channel 256x128x128 (reduced to 200 steps, K = 100)
+    # adjoint, porous channel 256x128x128, FP32, 2000 steps, checkpoints every 100
     nx, ny, nz = 256, 128, 128
-    m = I.channel(nx, ny, nz)
-    lat = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype="f32", scheme="pull")
-    lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 1)
-    lat.set_bgk(0.8)
-    lat.set_force((I.channel_force(ny, 0.8), 0, 0))
-    lat.set_porosity(torch.from_numpy(I.smoothed_porosity(2, m).reshape(-1)).cuda())
-    lat.init_equilibrium()
-    steps = 200
+    lat, m = porous_channel(olb, torch, nx, ny, nz, "f32")
     lat.adjoint_run(20, 10, (0, nx - 1, 0))
     torch.cuda.synchronize()
+    steps = 2000
     lat.init_equilibrium()
     t = time.perf_counter()
-    lat.adjoint_run(steps, 100, (0, nx - 1, 0))
+    loss, dg, dtau = lat.adjoint_run(steps, 100, (0, nx - 1, 0))
     torch.cuda.synchronize()
     sec = time.perf_counter() - t
     fl = int((m == I.FLUID).sum())
@@ -289,9 +283,80 @@ def variants(olb, torch):
     out["adjoint_channel256_f32"] = {
         "MLUPS": round(mlups, 1), "bytes_per_cell_step": 553,
         "roofline_frac": round(mlups * 1e6 * 553 / 1e9 / peak, 4),
-        "note": "forward + recompute + adjoint per cell-step, 200 steps, K=100"}
+        "loss": loss, "dL_dtau": dtau,
+        "note": "forward + recompute + adjoint per cell-step (553 B), 2000 steps, K=100, wall time"}
     lat.close()
     return out
+
+
+def porous_channel(olb, torch, nx, ny, nz, dtype, tau=0.8):
+    """The differentiable channel: periodic x, walls on y and z, smoothed porosity
+    (seed 2), Guo force for centre speed 0.05, at rest."""
+    m = I.channel(nx, ny, nz)
+    lat = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype=dtype, scheme="pull")
+    lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 1)
+    lat.set_bgk(tau)
+    lat.set_force((I.channel_force(ny, tau), 0, 0))
+    lat.set_porosity(torch.from_numpy(I.smoothed_porosity(2, m).reshape(-1)).cuda())
+    lat.init_equilibrium()
+    return lat, m
+
+
+def experiment_adjoint384(torch, olb, fd_cells=4):
+    """Adjoint at scale: channel 384x192x192, FP16 state (FP32 arithmetic, FP64
+    gradient), 4000 steps, checkpoints every 200; compared with the FP32-storage
+    adjoint (checkpoints every 100) and with central differences of FP64 forward
+    runs at `fd_cells` seeded fluid cells (h = 1e-5) and tau (h = 1e-6)."""
+    nx, ny, nz, steps = 384, 192, 192, 4000
+    obj = (0, nx - 1, 0)
+    res = {"workload": "channel 384x192x192, 4000 steps, loss = mean u_x on x = 383"}
+    grads = {}
+    for dtype, K in (("f16", 200), ("f32", 100)):
+        lat, m = porous_channel(olb, torch, nx, ny, nz, dtype)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        loss, dg, dtau = lat.adjoint_run(steps, K, obj)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t
+        fl = int((m == I.FLUID).sum())
+        grads[dtype] = (loss, dg.cpu().numpy().reshape(-1), dtau)
+        res[dtype] = {"K": K, "seconds": round(sec, 2), "MLUPS": round(fl * steps / sec / 1e6, 1),
+                      "loss": loss, "dL_dtau": dtau, "grad_l2": float(np.linalg.norm(grads[dtype][1]))}
+        lat.close()
+        del dg
+        torch.cuda.empty_cache()
+    g16, g32 = grads["f16"][1], grads["f32"][1]
+    res["f16_vs_f32_grad_rel_l2"] = float(np.linalg.norm(g16 - g32) / np.linalg.norm(g32))
+    res["f16_vs_f32_dtau_rel"] = abs(grads["f16"][2] - grads["f32"][2]) / abs(grads["f32"][2])
+    # FP64 central differences
+    m = I.channel(nx, ny, nz)
+    gamma = I.smoothed_porosity(2, m)
+    ref = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype="f64", scheme="pull")
+    ref.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 1)
+    ref.set_force((I.channel_force(ny, 0.8), 0, 0))
+    plane = torch.from_numpy(m[:, :, nx - 1] == I.FLUID).cuda()
+
+    def run(gam, tau):
+        ref.set_bgk(tau)
+        ref.set_porosity(torch.from_numpy(gam.reshape(-1)).cuda())
+        ref.init_equilibrium()
+        ref.step(steps)
+        _, u = ref.moments()
+        return float(u[0, :, :, nx - 1][plane].mean())
+
+    fd = []
+    for c in I.random_fluid_cells(3, m, fd_cells):
+        gp = gamma.reshape(-1).copy()
+        gm = gp.copy()
+        gp[c] += 1e-5
+        gm[c] -= 1e-5
+        d = (run(gp, 0.8) - run(gm, 0.8)) / 2e-5
+        fd.append({"cell": int(c), "fd": d, "f16_rel": abs(g16[c] - d) / abs(d), "f32_rel": abs(g32[c] - d) / abs(d)})
+    d = (run(gamma, 0.8 + 1e-6) - run(gamma, 0.8 - 1e-6)) / 2e-6
+    res["fd"] = fd
+    res["fd_dtau"] = {"fd": d, "f16_rel": abs(grads["f16"][2] - d) / abs(d), "f32_rel": abs(grads["f32"][2] - d) / abs(d)}
+    ref.close()
+    return res
 
 
 def run_ours(args):
@@ -438,7 +503,17 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--experiment", choices=["adjoint384"], default=None,
+                    help="run a named experiment instead of the benchmark and print its JSON")
     args = ap.parse_args()
+    if args.experiment == "adjoint384":
+        import torch
+
+        from paper_2307_11752_gb300 import build, olb
+        build.build()
+        olb.load()
+        print(json.dumps(experiment_adjoint384(torch, olb)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -836,7 +836,9 @@ __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p,
       const C usq = up[0] * up[0] + up[1] * up[1] + up[2] * up[2];
       const C m1u = m1[0] * up[0] + m1[1] * up[1] + m1[2] * up[2];
       const C um2u = up[0] * m2u[0] + up[1] * m2u[1] + up[2] * m2u[2];
-      const C A = m0 * (C(1) - C(1.5) * usq) + C(3) * m1u + C(4.5) * um2u;
+      // A - m0 (kept separately: the dL/domega term below needs it without the O(w) part)
+      const C Aex = C(3) * m1u + C(4.5) * um2u - C(1.5) * m0 * usq;
+      const C A = m0 + Aex;
       C B[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a)
@@ -856,12 +858,15 @@ __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p,
         lam_out[i * N + n.cell] = (typename LambdaOf<S>::T)((C(1) - om) * ls[i] + base + gi * Bc);
       }
       if (dgamma) dgamma[n.cell] += (double)Bu;
-      // dL/domega: -sum lam* f (unshifted f = shifted + w, so -lf - m0) + rho A - G/2
+      // dL/domega = sum_k lam*_k (feq_k - f_k) - G/2.  feq and f are both O(w) and
+      // differ by the small non-equilibrium part, so the O(w) parts are removed
+      // analytically before rounding: sum lam* (feq - w) = m0 drho + rho (A - m0)
+      // and sum lam* (f - w) = lf (f stored shifted).
       const C m1F = m1[0] * p.force[0] + m1[1] * p.force[1] + m1[2] * p.force[2];
       const C uF = up[0] * p.force[0] + up[1] * p.force[1] + up[2] * p.force[2];
       const C uM2F = up[0] * m2F[0] + up[1] * m2F[1] + up[2] * m2F[2];
       const C src_moment = C(3) * m1F - C(3) * m0 * uF + C(9) * uM2F;
-      sv[0] = -lf - m0 + rho * A - C(0.5) * src_moment;
+      sv[0] = m0 * drho + rho * Aex - lf - C(0.5) * src_moment;
     }
   }
   block_reduce_row(sv, partials + 8 * block_linear(), true);

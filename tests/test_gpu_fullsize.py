@@ -152,8 +152,8 @@ def test_channel_384_block_continuation_f16(oracle, olb):
     assert err <= 2e-3, err
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-6), ("f32", 2e-3)])
-def test_adjoint_channel256_matches_fp64_differences(olb, dtype, tol):
+@pytest.mark.parametrize("dtype,tol,tol_tau", [("f64", 1e-6, 1e-6), ("f32", 1e-3, 1e-4)])
+def test_adjoint_channel256_matches_fp64_differences(olb, dtype, tol, tol_tau):
     """Adjoint gradients on the 256 x 128 x 128 porous channel (100 steps, K = 25)
     against central differences of FP64 GPU forward runs at 3 seeded cells + tau."""
     import torch
@@ -203,5 +203,5 @@ def test_adjoint_channel256_matches_fp64_differences(olb, dtype, tol):
         assert abs(fd - dg[c]) <= tol * abs(fd) + 1e-11, (c, fd, dg[c])
     ht = 1e-6
     fd = (run(gamma, tau + ht) - run(gamma, tau - ht)) / (2 * ht)
-    assert abs(fd - dtau) <= tol * abs(fd), (fd, dtau)
+    assert abs(fd - dtau) <= tol_tau * abs(fd), (fd, dtau)
     ref.close()
