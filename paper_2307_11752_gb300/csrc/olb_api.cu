@@ -99,9 +99,9 @@ struct DevBuf {
 // starting addresses do not share all low address bits (a power-of-two lattice,
 // such as 128^3, would otherwise put the 19 loads of a warp at the same offset
 // modulo 2^23 bytes), keeping 256-byte alignment of every plane.
-// Row-group mapping of the paired step kernel (see k_step_pair).
-#ifndef OLB_ROW_GROUPS
-#define OLB_ROW_GROUPS 0
+// The step grid covers only the rows that hold fluid cells.
+#ifndef OLB_FLUID_BOX
+#define OLB_FLUID_BOX 1
 #endif
 
 #ifndef OLB_PLANE_PAD
@@ -223,6 +223,7 @@ struct olb_lattice {
   int cur = 0, repr = PRE, scheme = OLB_PULL;
   DevBuf mat, cls, wmask, pmask, word, wall_u, gamma, partials, out8;
   bool outside_links = false;
+  int y0 = 0, y1 = 0, z0 = 0, z1 = 0;  // bounding rows of the fluid cells
   std::vector<uint8_t> h_mat;
   unsigned periodic = 0;
   bool all_fluid = false, moving = false;
@@ -254,11 +255,15 @@ struct olb_lattice {
     p.pmask = static_cast<const uint32_t*>(pmask.p);
     p.word = static_cast<const uint32_t*>(word.p);
     p.outside_links = outside_links ? 1 : 0;
+    p.y0 = y0;
+    p.y1 = y1;
+    p.z0 = z0;
+    p.z1 = z1;
     p.stream = stream;
     return p;
   }
   // blocks (= rows of partial sums) of the step kernel and of the per-cell kernels
-  int64_t step_rows() const { return make_step_grid(nx, ny, nz, dtype != OLB_F64 && pairs_ok(nx)).blocks(); }
+  int64_t step_rows() const { return make_step_grid(params(), dtype != OLB_F64 && pairs_ok(nx)).blocks(); }
   int64_t cell_rows() const { return make_grid(nx, ny, nz).blocks(); }
   int64_t grid_blocks() const { return std::max(step_rows(), cell_rows()); }
 };
@@ -310,14 +315,13 @@ StepGrid make_step_grid(int nx, int ny, int nz, bool pairs) {
   g.tile_shift = shift;
   const int rows = 256 >> shift;
   g.gx = (units + (1 << shift) - 1) >> shift;
-  // paired kernel: whole rows per block when a row has 4 .. 256 pairs
-  const int P = nx / 2;
-  if (pairs && P >= 4 && P <= 256 && OLB_ROW_GROUPS) {
-    g.pair_rows = 256 / P;
-    g.row_blocks = ((int64_t)ny * nz + g.pair_rows - 1) / g.pair_rows;
-  }
   g.gy = (ny + rows - 1) / rows;
   g.nz = nz;
+  return g;
+}
+
+StepGrid make_step_grid(const HostParams& h, bool pairs) {
+  StepGrid g = make_step_grid(h.nx, h.y1 - h.y0 + 1, h.z1 - h.z0 + 1, pairs);
   return g;
 }
 
@@ -461,7 +465,7 @@ const char* olb_last_error(void) { return g_err.c_str(); }
 #define OLB_STR(x) OLB_STR2(x)
 const char* olb_build_info(void) {
   return "sm_103a step_min_blocks=" OLB_STR(OLB_STEP_MIN_BLOCKS) " pair_min_blocks=" OLB_STR(OLB_PAIR_MIN_BLOCKS) " pair16_min_blocks=" OLB_STR(OLB_PAIR16_MIN_BLOCKS)
-         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " row_groups=" OLB_STR(OLB_ROW_GROUPS) " xwall_pairs=" OLB_STR(OLB_XWALL_PAIRS) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
+         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " xwall_pairs=" OLB_STR(OLB_XWALL_PAIRS) " fluid_box=" OLB_STR(OLB_FLUID_BOX) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
 #ifdef OLB_NO_PAIRS
          " pairs=off"
 #else
@@ -590,6 +594,31 @@ int olb_set_material(olb_handle h, const uint8_t* material, unsigned periodic_ma
   h->moving = moving;
   h->outside_links = outside_links;
   h->all_fluid = !any_wall;
+  // rows that hold fluid cells; the step kernel skips the others (no cell there
+  // is updated, and their bounce-back slots are written by fluid neighbours)
+  int y0 = h->ny, y1 = -1, z0 = h->nz, z1 = -1;
+  for (int z = 0; z < h->nz; ++z)
+    for (int y = 0; y < h->ny; ++y) {
+      const uint8_t* row = h->h_mat.data() + ((int64_t)z * h->ny + y) * h->nx;
+      bool any = false;
+      for (int x = 0; x < h->nx && !any; ++x) any = row[x] == OLB_MAT_FLUID;
+      if (any) {
+        y0 = std::min(y0, y);
+        y1 = std::max(y1, y);
+        z0 = std::min(z0, z);
+        z1 = std::max(z1, z);
+      }
+    }
+  if (y1 < 0 || OLB_SOLID_FILL || !OLB_FLUID_BOX) {  // no fluid cell, or solid cells written too: full grid
+    y0 = 0;
+    y1 = h->ny - 1;
+    z0 = 0;
+    z1 = h->nz - 1;
+  }
+  h->y0 = y0;
+  h->y1 = y1;
+  h->z0 = z0;
+  h->z1 = z1;
   return upload_wall(h);
 }
 

@@ -41,6 +41,7 @@ struct HostParams {
   const uint32_t* pmask;  // per cell: bit i set when x + c_i is a non-fluid cell of the lattice
   const uint32_t* word;   // per cell link word of the step kernel
   int outside_links;      // some fluid cell has a link leaving the domain
+  int y0, y1, z0, z1;     // rows holding fluid cells: y in [y0, y1], z in [z0, z1]
   cudaStream_t stream;
 };
 
@@ -56,12 +57,12 @@ Grid make_grid(int nx, int ny, int nz);
 // neighbouring cells (x0, x0 + 1) in the paired kernel.
 struct StepGrid {
   int gx, gy, nz, tile_shift;
-  int pair_rows = 0;    // paired kernel: rows per block (row-group mapping), 0 = tiles
-  int64_t row_blocks = 0;
-  int64_t blocks() const { return pair_rows > 0 ? row_blocks : (int64_t)gx * gy * nz; }
-  dim3 dims() const { return pair_rows > 0 ? dim3((unsigned)row_blocks, 1, 1) : dim3(gx, gy, nz); }
+  int64_t blocks() const { return (int64_t)gx * gy * nz; }
+  dim3 dims() const { return dim3(gx, gy, nz); }
 };
 StepGrid make_step_grid(int nx, int ny, int nz, bool pairs);
+// Step grid restricted to the rows y in [y0, y1], z in [z0, z1].
+StepGrid make_step_grid(const HostParams& h, bool pairs);
 // The paired kernel runs for FP32-arithmetic storage types when nx is even.
 #ifdef OLB_NO_PAIRS
 inline bool pairs_ok(int) { return false; }

@@ -42,6 +42,11 @@
 #ifndef OLB_PAIR_MIN_BLOCKS
 #define OLB_PAIR_MIN_BLOCKS 2
 #endif
+// Use the boundary-capable instance of the paired kernel on every lattice (for
+// measuring what the boundary code costs on lattices without walls).
+#ifndef OLB_FORCE_WALLS
+#define OLB_FORCE_WALLS 0
+#endif
 #ifndef OLB_PAIR16_MIN_BLOCKS
 #define OLB_PAIR16_MIN_BLOCKS 3
 #endif
@@ -153,9 +158,9 @@ struct Params {
   // per cell link word of the step kernel (see kWordFluid)
   const uint32_t* __restrict__ word;
   int outside_links;  // some fluid cell has a link leaving the domain
-  // step-kernel grid: gx * gy * nz tiles of (1 << tile_shift) x (256 >> tile_shift),
-  // or, for the paired kernel with pair_rows > 0, blocks of pair_rows whole rows
-  int gx, gy, tile_shift, pair_rows;
+  // step-kernel grid: gx * gy * nz tiles of (1 << tile_shift) x (256 >> tile_shift)
+  int gx, gy, tile_shift;
+  int y0, z0, y1, z1;  // rows covered by the step grid
 };
 
 template <class C>
@@ -183,11 +188,14 @@ Params<C> to_params(const HostParams& h) {
   p.pmask = h.pmask;
   p.word = h.word;
   p.outside_links = h.outside_links;
-  const StepGrid sg = make_step_grid(h.nx, h.ny, h.nz, false);
+  p.y0 = h.y0;
+  p.y1 = h.y1;
+  p.z0 = h.z0;
+  p.z1 = h.z1;
+  const StepGrid sg = make_step_grid(h, false);
   p.gx = sg.gx;
   p.gy = sg.gy;
   p.tile_shift = sg.tile_shift;
-  p.pair_rows = 0;
   return p;
 }
 
@@ -558,10 +566,10 @@ __global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typena
   using C = typename Store<S>::C;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
   const int tid = threadIdx.x;
-  const int z = blockIdx.z;
+  const int z = p.z0 + blockIdx.z;
   const int x = (blockIdx.x << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1));
-  const int y = blockIdx.y * (256 >> p.tile_shift) + (tid >> p.tile_shift);
-  if (x < p.nx && y < p.ny) {
+  const int y = p.y0 + blockIdx.y * (256 >> p.tile_shift) + (tid >> p.tile_shift);
+  if (x < p.nx && y <= p.y1) {
     const Nbr n = make_nbr<L>(p, x, y, z);
     const uint32_t w = p.all_fluid ? kWordFluid : p.word[n.cell];
     C f[L::Q];
@@ -935,26 +943,25 @@ struct Launch {
   static cudaError_t step_t(const HostParams& h, const void* src, void* dst, double* partials) {
     if constexpr (!std::is_same<S, double>::value) {
       if (pairs_ok(h.nx)) {
-        const StepGrid g = make_step_grid(h.nx, h.ny, h.nz, true);
+        const StepGrid g = make_step_grid(h, true);
         Params<float> p = params(h);
         p.gx = g.gx;
         p.gy = g.gy;
         p.tile_shift = g.tile_shift;
-        p.pair_rows = g.pair_rows;
         Planes<S> pl;
         for (int i = 0; i < 19; ++i) {
           const int k = i < L::Q ? i : 0;
           pl.src[i] = static_cast<const S*>(src) + (size_t)k * h.pitch;
           pl.dst[i] = static_cast<S*>(dst) + (size_t)k * h.pitch;
         }
-        if (h.cls == nullptr)  // all fluid, all periodic
+        if (h.cls == nullptr && !OLB_FORCE_WALLS)  // all fluid, all periodic
           k_step_pair<L, S, G, SC, STATS, false><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
         else
           k_step_pair<L, S, G, SC, STATS, true><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
         return cudaGetLastError();
       }
     }
-    const StepGrid g = make_step_grid(h.nx, h.ny, h.nz, false);
+    const StepGrid g = make_step_grid(h, false);
     k_step<L, S, G, SC, STATS><<<g.dims(), 256, 0, h.stream>>>(
         params(h), static_cast<const S*>(src), static_cast<S*>(dst), partials);
     return cudaGetLastError();

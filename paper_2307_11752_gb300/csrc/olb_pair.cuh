@@ -291,32 +291,11 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
   const int tid = threadIdx.x;
   int x0, y, z;
   bool active;
-  if (p.pair_rows > 0) {
-    // Row-group mapping: the block updates pair_rows whole rows of P = nx/2 pairs.
-    // Threads [0, R (P-2)) take the inner pairs 1 .. P-2 row by row; the last 2R
-    // threads take the first and last pair of each row -- the ones next to walls
-    // on the x faces -- so that only the block's last warp runs their code.
-    const int P = p.nx >> 1, R = p.pair_rows;
-    const int inner = P - 2;
-    int r, q;
-    if (tid < R * inner) {
-      r = tid / inner;
-      q = 1 + (tid - r * inner);
-    } else {
-      const int e = tid - R * inner;
-      r = e >> 1;
-      q = (e & 1) ? P - 1 : 0;
-    }
-    const int row = (int)block_linear() * R + r;
-    active = tid < R * P && row < p.ny * p.nz;
-    y = row % p.ny;
-    z = row / p.ny;
-    x0 = 2 * q;
-  } else {
-    z = blockIdx.z;
+  {
+    z = p.z0 + blockIdx.z;
     x0 = 2 * ((blockIdx.x << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1)));
-    y = blockIdx.y * (256 >> p.tile_shift) + (tid >> p.tile_shift);
-    active = x0 < p.nx && y < p.ny;
+    y = p.y0 + blockIdx.y * (256 >> p.tile_shift) + (tid >> p.tile_shift);
+    active = x0 < p.nx && y <= p.y1;
   }
   if (active) {
     const PairNbr n = make_pair_nbr<L>(p, x0, y, z);
