@@ -1,0 +1,57 @@
+"""Failure injection on the host (no GPU needed): the device-memory provider
+returns NULL, as an exhausted allocator would, and the library reports
+OLB_ERR_OOM with a message instead of crashing; argument errors that are
+detected before any CUDA call return OLB_ERR_ARG."""
+import ctypes
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2307_11752_gb300 import build, olb
+    build.build()
+    return olb.load()
+
+
+def test_allocator_failure_is_reported_as_oom(lib):
+    from paper_2307_11752_gb300 import olb
+
+    calls = []
+
+    @olb._ALLOC_T
+    def failing_alloc(size, ctx):
+        calls.append(size)
+        return None
+
+    @olb._FREE_T
+    def never_free(ptr, ctx):
+        raise AssertionError("nothing was allocated")
+
+    assert lib.olb_set_allocator(ctypes.cast(failing_alloc, ctypes.c_void_p),
+                                 ctypes.cast(never_free, ctypes.c_void_p), None) == 0
+    try:
+        h = ctypes.c_void_p()
+        rc = lib.olb_lattice_create(olb.D3Q19, 16, 16, 16, olb.F32, ctypes.byref(h))
+        assert rc == -3
+        assert h.value is None
+        assert "allocator returned no memory" in lib.olb_last_error().decode()
+        assert calls and calls[0] == 19 * (16 ** 3 + 256) * 4  # the first population buffer
+    finally:
+        assert lib.olb_set_allocator(None, None, None) == 0
+
+
+def test_arguments_rejected_before_any_device_call(lib):
+    from paper_2307_11752_gb300 import olb
+
+    h = ctypes.c_void_p()
+    assert lib.olb_lattice_create(olb.D2Q9, 8, 8, 2, olb.F32, ctypes.byref(h)) == -1
+    assert "nz == 1" in lib.olb_last_error().decode()
+    assert lib.olb_lattice_create(5, 8, 8, 1, olb.F32, ctypes.byref(h)) == -1
+    assert lib.olb_lattice_create(olb.D3Q19, 0, 8, 8, olb.F32, ctypes.byref(h)) == -1
+    assert lib.olb_lattice_create(olb.D3Q19, 8, 8, 8, 9, ctypes.byref(h)) == -1
+    assert lib.olb_lattice_create(olb.D3Q19, 8, 8, 8, olb.F32, None) == -1
+    assert lib.olb_set_bgk(None, 0.8) == -1
+    assert lib.olb_step(None, 1) == -1
+    assert lib.olb_lattice_destroy(None) == -1
+    assert lib.olb_set_allocator(ctypes.c_void_p(1), None, None) == -1  # alloc without free
