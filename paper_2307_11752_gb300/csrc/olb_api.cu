@@ -168,8 +168,9 @@ void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, u
           word[c] = nb;
           continue;
         }
-        bool moving_link = false;
-        uint32_t wm = 0, pm = 0;
+        bool moving_link = false, mixed = false;
+        uint32_t wm = 0, pm = 0, mv = 0;
+        int mm = -1;  // material of the moving links
         bool out = false;
         for (int i = 1; i < L::Q; ++i) {
           for (int sgn = -1; sgn <= 1; sgn += 2) {  // -1: pull source x - c_i, +1: push target x + c_i
@@ -189,7 +190,12 @@ void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, u
               if (sgn < 0) wm |= 1u << i;
               if (sgn > 0 && inside) {
                 pm |= 1u << i;
-                if (nm >= 3) *moving = moving_link = true;
+                if (nm >= 3) {
+                  *moving = moving_link = true;
+                  mv |= 1u << i;
+                  if (mm >= 0 && mm != nm) mixed = true;
+                  mm = nm;
+                }
               }
               if (!inside) out = true;
             }
@@ -197,7 +203,16 @@ void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, u
         }
         wmask[c] = wm;
         pmask[c] = pm;
-        word[c] = kWordFluid | (moving_link ? kWordMoving : 0u) | pm;
+        uint32_t plane = 0;  // plane form of the moving links (see kWordPlaneShift)
+        for (int ax = 0; moving_link && !mixed && ax < L::DIM && !plane; ++ax)
+          for (int s = -1; s <= 1 && !plane; s += 2) {
+            uint32_t sel = 0;
+            for (int i = 1; i < L::Q; ++i)
+              if (((pm >> i) & 1u) && L::c(i, ax) == s) sel |= 1u << i;
+            if (sel == mv) plane = 1u + 2u * ax + (s > 0 ? 1u : 0u);
+          }
+        word[c] = kWordFluid | (moving_link ? kWordMoving : 0u) | pm |
+                  (plane ? (plane << kWordPlaneShift) | ((uint32_t)mm << kWordMatShift) : 0u);
         cls[c] = out ? 3 : (wm ? 2 : 1);
         if (out) *outside_links = true;
         if (wm) *any_wall = true;
@@ -228,6 +243,7 @@ struct olb_lattice {
   unsigned periodic = 0;
   bool all_fluid = false, moving = false;
   double h_wall[256][4];
+  float h_wall_f[256][20];  // 6 w_i (c_i . u_w), computed in FP64 and rounded once
   double tau = 1.0, F[3] = {0.0, 0.0, 0.0};
   bool has_gamma = false;
   int64_t time = 0, launches = 0;
@@ -247,6 +263,7 @@ struct olb_lattice {
     p.wmask = static_cast<const uint32_t*>(wmask.p);
     p.mat = static_cast<const uint8_t*>(mat.p);
     p.wall_u = static_cast<const double*>(wall_u.p);
+    p.wall_f = reinterpret_cast<const float*>(static_cast<const char*>(wall_u.p) + sizeof(h_wall));
     p.moving = moving ? 1 : 0;
     p.omega = 1.0 / tau;
     for (int a = 0; a < 3; ++a) p.force[a] = F[a];
@@ -445,10 +462,32 @@ int deliver_stats(olb_handle h, double* out) {
   return OLB_OK;
 }
 
+template <class L>
+void wall_terms(olb_handle h) {
+  for (int m = 0; m < 256; ++m) {
+    const double* u = h->h_wall[m];
+    for (int i = 0; i < 20; ++i) {
+      if (i >= L::Q) {
+        h->h_wall_f[m][i] = 0.0f;
+        continue;
+      }
+      const double cu = L::c(i, 0) * u[0] + L::c(i, 1) * u[1] + L::c(i, 2) * u[2];
+      h->h_wall_f[m][i] = (float)(6.0 * L::w(i) * cu);
+    }
+  }
+}
+
 int upload_wall(olb_handle h) {
+  if (h->desc == OLB_D2Q9)
+    wall_terms<D2Q9>(h);
+  else
+    wall_terms<D3Q19>(h);
   OLB_CUDA(cudaMemcpyAsync(h->wall_u.p, h->h_wall, sizeof(h->h_wall), cudaMemcpyHostToDevice,
                            h->stream),
            "wall velocity upload");
+  OLB_CUDA(cudaMemcpyAsync(static_cast<char*>(h->wall_u.p) + sizeof(h->h_wall), h->h_wall_f,
+                           sizeof(h->h_wall_f), cudaMemcpyHostToDevice, h->stream),
+           "wall term upload");
   return OLB_OK;
 }
 
@@ -464,7 +503,7 @@ const char* olb_last_error(void) { return g_err.c_str(); }
 #define OLB_STR2(x) #x
 #define OLB_STR(x) OLB_STR2(x)
 const char* olb_build_info(void) {
-  return "sm_103a step_min_blocks=" OLB_STR(OLB_STEP_MIN_BLOCKS) " pair_min_blocks=" OLB_STR(OLB_PAIR_MIN_BLOCKS) " pair16_min_blocks=" OLB_STR(OLB_PAIR16_MIN_BLOCKS)
+  return "sm_103a step_min_blocks=" OLB_STR(OLB_STEP_MIN_BLOCKS) " pair_min_blocks=" OLB_STR(OLB_PAIR_MIN_BLOCKS) " pair16_min_blocks=" OLB_STR(OLB_PAIR16_MIN_BLOCKS) " pair16_walls_min_blocks=" OLB_STR(OLB_PAIR16_WALLS_MIN_BLOCKS) " ghost16=" OLB_STR(OLB_GHOST_FIRST16) OLB_STR(OLB_GHOST_COORDS16) " ghost32=" OLB_STR(OLB_GHOST_FIRST32) OLB_STR(OLB_GHOST_COORDS32)
          " solid_fill=" OLB_STR(OLB_SOLID_FILL) " xwall_pairs=" OLB_STR(OLB_XWALL_PAIRS) " fluid_box=" OLB_STR(OLB_FLUID_BOX) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
 #ifdef OLB_NO_PAIRS
          " pairs=off"
@@ -511,7 +550,7 @@ int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, ol
   if ((rc = h->buf[0].reserve(h->state_bytes())) || (rc = h->mat.reserve(cells)) ||
       (rc = h->cls.reserve(cells)) || (rc = h->wmask.reserve(cells * 4)) || (rc = h->pmask.reserve(cells * 4)) ||
       (rc = h->word.reserve(cells * 4)) ||
-      (rc = h->wall_u.reserve(sizeof(h->h_wall))) ||
+      (rc = h->wall_u.reserve(sizeof(h->h_wall) + sizeof(h->h_wall_f))) ||
       (rc = ensure_partials(h, h->grid_blocks()))) {
     std::string msg = g_err;
     delete h;

@@ -33,6 +33,7 @@ struct HostParams {
   const uint32_t* wmask;  // per cell: bit i set when the pull source x - c_i is not a fluid cell
   const uint8_t* mat;     // material numbers
   const double* wall_u;   // [256][4] moving-wall velocities
+  const float* wall_f;    // [256][20] 6 w_i (c_i . u_w) per material and direction, FP32
   int moving;             // a moving-wall material touches the fluid
   double omega;
   double force[3];

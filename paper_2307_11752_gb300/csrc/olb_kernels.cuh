@@ -50,6 +50,26 @@
 #ifndef OLB_PAIR16_MIN_BLOCKS
 #define OLB_PAIR16_MIN_BLOCKS 3
 #endif
+// 16-bit storage, instance with boundary code (more live values than the
+// all-fluid instance: at 3 blocks it spills).
+#ifndef OLB_PAIR16_WALLS_MIN_BLOCKS
+#define OLB_PAIR16_WALLS_MIN_BLOCKS 3
+#endif
+// Order and addressing of the bounce-back stores of the paired kernel, per storage
+// width: FIRST = before the own-slot stores (fewer live registers), COORDS = the
+// target index rebuilt from the coordinates instead of kept from the loads.
+#ifndef OLB_GHOST_FIRST16
+#define OLB_GHOST_FIRST16 1
+#endif
+#ifndef OLB_GHOST_COORDS16
+#define OLB_GHOST_COORDS16 1
+#endif
+#ifndef OLB_GHOST_FIRST32
+#define OLB_GHOST_FIRST32 0
+#endif
+#ifndef OLB_GHOST_COORDS32
+#define OLB_GHOST_COORDS32 0
+#endif
 
 namespace olb {
 
@@ -96,6 +116,13 @@ __host__ __device__ constexpr int opp(int i) {
 constexpr uint32_t kWordFluid = 1u << 31;
 constexpr uint32_t kWordMoving = 1u << 30;  // a bounce-back link hits a moving wall
 constexpr uint32_t kWordLinks = (1u << 19) - 1;
+// Moving links of a fluid cell in plane form (bits 19..29): when the moving links
+// are exactly the wall links with c_i[a] == s and all hit one material m, bits
+// 19..21 hold 1 + 2a + (s > 0) and bits 22..29 hold m; the step kernel then takes
+// the wall term from the cell's own word instead of loading each neighbour's
+// material.  Plane code 0: load the materials (any other arrangement).
+constexpr int kWordPlaneShift = 19;
+constexpr int kWordMatShift = 22;
 
 // Non-fluid cells also store zeros into the slots that no fluid neighbour fills,
 // so that every memory sector of a step's output is written in full.
@@ -161,6 +188,7 @@ struct Params {
   // step-kernel grid: gx * gy * nz tiles of (1 << tile_shift) x (256 >> tile_shift)
   int gx, gy, tile_shift;
   int y0, z0, y1, z1;  // rows covered by the step grid
+  const float* __restrict__ wall_f;  // [256][20]: 6 w_i (c_i . u_w) rounded once to FP32
 };
 
 template <class C>
@@ -177,6 +205,7 @@ Params<C> to_params(const HostParams& h) {
   p.wmask = h.wmask;
   p.mat = h.mat;
   p.wall_u = h.wall_u;
+  p.wall_f = h.wall_f;
   p.moving = h.moving;
   p.omega = (C)h.omega;
   for (int a = 0; a < 3; ++a) {
@@ -252,12 +281,20 @@ __device__ __forceinline__ int link_material(const Params<C>& p, const Nbr& n, i
   return p.mat[(q[2] * p.ny + q[1]) * p.nx + q[0]];
 }
 
-// 6 w_i (c_i . u_w) of wall material m.
+// 6 w_i (c_i . u_w) of wall material m.  The FP32 paths read it from the table
+// the host fills when a wall velocity is set (the same double expression, rounded
+// once), so that no FP64 instruction runs in them: FP64 issues at a small fraction
+// of the FP32 rate on sm_103a, and the cells next to a moving wall sit together in
+// the last blocks of the grid, where that work would lengthen the kernel's tail.
 template <class L, class C>
 __device__ __forceinline__ C wall_term(const Params<C>& p, int i, int m) {
-  const double* u = p.wall_u + 4 * m;
-  double cu = L::c(i, 0) * u[0] + L::c(i, 1) * u[1] + L::c(i, 2) * u[2];
-  return (C)(6.0 * L::w(i) * cu);
+  if constexpr (sizeof(C) == sizeof(float)) {
+    return p.wall_f[20 * m + i];
+  } else {
+    const double* u = p.wall_u + 4 * m;
+    double cu = L::c(i, 0) * u[0] + L::c(i, 1) * u[1] + L::c(i, 2) * u[2];
+    return (C)(6.0 * L::w(i) * cu);
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -948,16 +985,23 @@ struct Launch {
         p.gx = g.gx;
         p.gy = g.gy;
         p.tile_shift = g.tile_shift;
-        Planes<S> pl;
-        for (int i = 0; i < 19; ++i) {
-          const int k = i < L::Q ? i : 0;
-          pl.src[i] = static_cast<const S*>(src) + (size_t)k * h.pitch;
-          pl.dst[i] = static_cast<S*>(dst) + (size_t)k * h.pitch;
-        }
-        if (h.cls == nullptr && !OLB_FORCE_WALLS)  // all fluid, all periodic
+        auto fill = [&](auto& pl) {
+          for (int i = 0; i < 19; ++i) {
+            const int k = i < L::Q ? i : 0;
+            pl.src[i] = static_cast<const S*>(src) + (size_t)k * h.pitch;
+            pl.dst[i] = static_cast<S*>(dst) + (size_t)k * h.pitch;
+          }
+        };
+        if (h.cls == nullptr && !OLB_FORCE_WALLS) {  // all fluid, all periodic
+          Planes<S, false> pl;
+          fill(pl);
           k_step_pair<L, S, G, SC, STATS, false><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
-        else
+        } else {
+          Planes<S, true> pl;
+          pl.lead = 0;
+          fill(pl);
           k_step_pair<L, S, G, SC, STATS, true><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
+        }
         return cudaGetLastError();
       }
     }

@@ -43,6 +43,9 @@ template <>
 struct PairStore<float> {
   static constexpr float SCALE = 1.0f;
   static constexpr int MIN_BLOCKS = OLB_PAIR_MIN_BLOCKS;
+  static constexpr int MIN_BLOCKS_WALLS = OLB_PAIR_MIN_BLOCKS;
+  static constexpr bool GHOST_FIRST = OLB_GHOST_FIRST32;
+  static constexpr bool GHOST_COORDS = OLB_GHOST_COORDS32;
   __device__ static float ld1(const float* p) { return *p; }
   __device__ static F2 ld2(const float* p) { return F2(*reinterpret_cast<const float2*>(p)); }
   __device__ static void st1(float* p, float v) { *p = v; }
@@ -52,6 +55,9 @@ template <>
 struct PairStore<__half> {
   static constexpr float SCALE = Store<__half>::kScale;
   static constexpr int MIN_BLOCKS = OLB_PAIR16_MIN_BLOCKS;
+  static constexpr int MIN_BLOCKS_WALLS = OLB_PAIR16_WALLS_MIN_BLOCKS;
+  static constexpr bool GHOST_FIRST = OLB_GHOST_FIRST16;
+  static constexpr bool GHOST_COORDS = OLB_GHOST_COORDS16;
   __device__ static float ld1(const __half* p) { return __half2float(*p); }
   __device__ static F2 ld2(const __half* p) { return F2(__half22float2(*reinterpret_cast<const __half2*>(p))); }
   __device__ static void st1(__half* p, float v) { *p = __float2half_rn(v); }
@@ -61,6 +67,9 @@ template <>
 struct PairStore<__nv_bfloat16> {
   static constexpr float SCALE = 1.0f;
   static constexpr int MIN_BLOCKS = OLB_PAIR16_MIN_BLOCKS;
+  static constexpr int MIN_BLOCKS_WALLS = OLB_PAIR16_WALLS_MIN_BLOCKS;
+  static constexpr bool GHOST_FIRST = OLB_GHOST_FIRST16;
+  static constexpr bool GHOST_COORDS = OLB_GHOST_COORDS16;
   __device__ static float ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   __device__ static F2 ld2(const __nv_bfloat16* p) {
     return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)));
@@ -75,8 +84,23 @@ struct PairStore<__nv_bfloat16> {
 // passed as kernel parameters: each access is then one index add and one wide
 // multiply-add on a constant-bank operand, instead of recomputing
 // buffer + slot * pitch per access.
+//
+// The pointers' offset in the parameter space changes the generated code, and the
+// instances differ in which offset they run faster with (measured at 128^3): the
+// all-fluid FP32 step took 18% longer with its pointers at 8 mod 16 bytes than at
+// 0 mod 16, while the instances with walls ran 1-3% faster at 8 mod 16.  So the
+// struct is 16-byte aligned and LEAD = true puts one 8-byte word before the
+// pointers; each instance takes its offset from that, not from sizeof(Params).
+template <class S, bool LEAD>
+struct alignas(16) Planes;
 template <class S>
-struct Planes {
+struct alignas(16) Planes<S, false> {
+  const S* src[19];
+  S* dst[19];
+};
+template <class S>
+struct alignas(16) Planes<S, true> {
+  unsigned long long lead;
   const S* src[19];
   S* dst[19];
 };
@@ -231,11 +255,44 @@ __device__ __forceinline__ void collide_pair(const Params<float>& p, F2 gamma, F
   }
 }
 
-// 6 w_i (c_i . u_w) of wall material m (FP32).
+// 6 w_i (c_i . u_w) of wall material m (FP32 table).
 template <class L>
 __device__ __forceinline__ float wall_term_f(const Params<float>& p, int i, int m) {
-  const double* uw = p.wall_u + 4 * m;
-  return (float)(6.0 * L::w(i) * (L::c(i, 0) * uw[0] + L::c(i, 1) * uw[1] + L::c(i, 2) * uw[2]));
+  return p.wall_f[20 * m + i];
+}
+
+// Moving-wall part of the bounce-back of link i of a fluid cell with link word
+// `word` (kWordMoving set): true and 6 w_i (c_i . u_w) in `t` when x + c_i is a
+// moving wall.  The plane form of the word answers without a load; otherwise the
+// neighbour's material is read.  tx indexes PairNbr::xs for x + c_i.
+template <class L>
+__device__ __forceinline__ bool moving_term(const Params<float>& p, int target, int i, uint32_t word, float& t) {
+  const uint32_t code = (word >> kWordPlaneShift) & 7u;
+  if (code) {
+    const int a = (int)(code - 1) >> 1;
+    const int s = (code & 1u) ? -1 : 1;
+    const int ca = a == 0 ? L::c(i, 0) : (a == 1 ? L::c(i, 1) : L::c(i, 2));
+    t = wall_term_f<L>(p, i, (int)((word >> kWordMatShift) & 255u));
+    return ca == s;
+  }
+  const int wm = p.mat[target];
+  if (wm < 3) return false;
+  t = wall_term_f<L>(p, i, wm);
+  return true;
+}
+
+// Index of the cell (x + dx, y + dy, z + dz), wrapped on every axis (a bounce-back
+// link that crosses a lattice face crosses a periodic one: on the others the
+// target is outside the lattice and the link is not a bounce-back link).  Built
+// from the coordinates, so that the rare store paths that need it keep no
+// neighbour indices live through the collision.
+template <class L>
+__device__ __forceinline__ int wrapped_cell(const Params<float>& p, int x, int y, int z, int dx, int dy, int dz) {
+  int xt = x + dx, yt = y + dy, zt = z + dz;
+  if (dx) xt = xt < 0 ? xt + p.nx : (xt >= p.nx ? xt - p.nx : xt);
+  if (dy) yt = yt < 0 ? yt + p.ny : (yt >= p.ny ? yt - p.ny : yt);
+  if (L::DIM == 3 && dz) zt = zt < 0 ? zt + p.nz : (zt >= p.nz ? zt - p.nz : zt);
+  return (zt * p.ny + yt) * p.nx + xt;
 }
 
 // Special store paths for pairs at walls on the x faces (see the store phase).
@@ -255,21 +312,20 @@ __host__ __device__ constexpr uint32_t dir_mask(int cx) {
 
 // Bounce-back stores of cell h of a pair for the links set in `l`, testing only
 // the directions with c_x == CX (CX == 0: all directions).
-template <class L, class S, int SC, int CX>
-__device__ __forceinline__ void ghost_stores(const Params<float>& p, const Planes<S>& pl, const PairNbr& n, int h,
-                                             uint32_t l, uint32_t word, const F2 (&f)[L::Q], F2 rho) {
+template <class L, class S, int SC, int CX, bool COORDS, class P>
+__device__ __forceinline__ void ghost_stores(const Params<float>& p, const P& pl, const PairNbr& n, int h, int y,
+                                             int z, uint32_t l, uint32_t word, float fh[L::Q], float rh) {
 #pragma unroll
   for (int i = 1; i < L::Q; ++i) {
     if (CX != 0 && L::c(i, 0) != CX) continue;
     if (l & (1u << i)) {
-      const int tx = 1 + h + L::c(i, 0);  // index into xs of x + c_i
-      float v = h == 0 ? f[i].v.x : f[i].v.y;
-      if (word & kWordMoving) {
-        const int wm = p.mat[n.at(tx, L::c(i, 1), L::c(i, 2))];
-        if (wm >= 3) v -= (h == 0 ? rho.v.x : rho.v.y) * wall_term_f<L>(p, i, wm);  // rho_s 6 w c.u_w
-      }
+      const int target = COORDS ? wrapped_cell<L>(p, n.x0 + h, y, z, L::c(i, 0), L::c(i, 1), L::c(i, 2))
+                                : n.at(1 + h + L::c(i, 0), L::c(i, 1), L::c(i, 2));
+      float v = fh[i];
+      float t;
+      if ((word & kWordMoving) && moving_term<L>(p, target, i, word, t)) v -= rh * t;  // rho_s 6 w c.u_w
       const int slot = (SC == S_OWN) ? opp<L>(i) : i;
-      PairStore<S>::st1(pl.dst[slot] + n.at(tx, L::c(i, 1), L::c(i, 2)), v);
+      PairStore<S>::st1(pl.dst[slot] + target, v);
     }
   }
 }
@@ -282,8 +338,8 @@ __device__ __forceinline__ void ghost_stores(const Params<float>& p, const Plane
 // the boundary paths cannot cost registers or scheduling freedom there.
 // ---------------------------------------------------------------------------------
 template <class L, class S, int G, int SC, bool STATS, bool WALLS>
-__global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Params<float> p,
-                                                                             const __grid_constant__ Planes<S> pl,
+__global__ void __launch_bounds__(256, WALLS ? PairStore<S>::MIN_BLOCKS_WALLS : PairStore<S>::MIN_BLOCKS) k_step_pair(Params<float> p,
+                                                                             const __grid_constant__ Planes<S, WALLS> pl,
                                                                              double* partials) {
   constexpr int SC_NUM = (int)PairStore<S>::SCALE;
   constexpr float INV_SCALE = 1.0f / PairStore<S>::SCALE;
@@ -361,6 +417,35 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
       const uint32_t nb0 = w[0] & kWordLinks, nb1 = w[1] & kWordLinks;
       const bool lo = OLB_XWALL_PAIRS && !fl0 && fl1 && !(nb0 & ~dir_mask<L>(1));   // non-fluid x0, fluid x0 + 1
       const bool hi = OLB_XWALL_PAIRS && fl0 && !fl1 && !(nb1 & ~dir_mask<L>(-1));  // fluid x0, non-fluid x0 + 1
+      // Bounce-back links: the bounced population goes into the wall cell x + c_i,
+      // in the slot that x reads there at the next step.  A cell next to a wall on
+      // an x face has its links only among the 5 directions with c_x = -1 (or +1);
+      // it tests only those.  These slots are never among the own slots stored
+      // below (see above), so the bounce-back stores go first: the own-slot stores
+      // then release the post-collision values one by one.
+      const uint32_t l0 = fl0 ? nb0 : 0u;
+      const uint32_t l1 = fl1 ? nb1 : 0u;
+      auto bounce_back = [&]() {
+      if (l0 | l1) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t l = h == 0 ? l0 : l1;
+          if (l) {
+            float fh[L::Q];
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) fh[i] = h == 0 ? f[i].v.x : f[i].v.y;
+            const float rh = h == 0 ? rho.v.x : rho.v.y;
+            if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(-1)))
+              ghost_stores<L, S, SC, -1, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
+            else if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(1)))
+              ghost_stores<L, S, SC, 1, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
+            else
+              ghost_stores<L, S, SC, 0, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
+          }
+        }
+      }
+      };
+      if (PairStore<S>::GHOST_FIRST) bounce_back();
       if ((fl0 && fl1) || lo || hi) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
@@ -381,26 +466,7 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
           if (fl1) PairStore<S>::st1(q + 1, f[i].v.y);
         }
       }
-      // Bounce-back links: the bounced population goes into the wall cell x + c_i,
-      // in the slot that x reads there at the next step.  A cell next to a wall on
-      // an x face has its links only among the 5 directions with c_x = -1 (or +1);
-      // it tests only those.
-      const uint32_t l0 = fl0 ? nb0 : 0u;
-      const uint32_t l1 = fl1 ? nb1 : 0u;
-      if (l0 | l1) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t l = h == 0 ? l0 : l1;
-          if (l) {
-            if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(-1)))
-              ghost_stores<L, S, SC, -1>(p, pl, n, h, l, w[h], f, rho);
-            else if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(1)))
-              ghost_stores<L, S, SC, 1>(p, pl, n, h, l, w[h], f, rho);
-            else
-              ghost_stores<L, S, SC, 0>(p, pl, n, h, l, w[h], f, rho);
-          }
-        }
-      }
+      if (!PairStore<S>::GHOST_FIRST) bounce_back();
       if (OLB_SOLID_FILL) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -439,10 +505,10 @@ __global__ void __launch_bounds__(256, PairStore<S>::MIN_BLOCKS) k_step_pair(Par
               const bool out = i != 0 && edge[h] && outside(p, c1, L::c(i, 0), L::c(i, 1), L::c(i, 2));
               if (wall || out) {
                 float bounced = fi;
-                if (wall && (wd & kWordMoving)) {
-                  const int wm = p.mat[n.at(tx, L::c(i, 1), L::c(i, 2))];
-                  if (wm >= 3) bounced -= rh * wall_term_f<L>(p, i, wm);
-                }
+                float t;
+                if (wall && (wd & kWordMoving) &&
+                    moving_term<L>(p, n.at(tx, L::c(i, 1), L::c(i, 2)), i, wd, t))
+                  bounced -= rh * t;
                 PairStore<S>::st1(pl.dst[opp<L>(i)] + c, bounced);
               } else {
                 PairStore<S>::st1(pl.dst[i] + n.at(tx, L::c(i, 1), L::c(i, 2)), fi);

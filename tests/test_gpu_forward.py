@@ -74,6 +74,23 @@ def test_porous_channel_with_moving_wall_d2q9(oracle, olb, dtype):
     _compare(oracle, porous_channel_case(nx=45, ny=13, d=0, moving=True), 91, dtype, "aa")
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_moving_walls_beyond_the_plane_form(oracle, olb, dtype, scheme):
+    """Moving links that the link word cannot hold in plane form, next to cells
+    whose links it can: a lid that stops short of the z edges (cells at its rim
+    have links with c_y = +1 to the lid and to a fixed wall) and a second moving
+    face x = nx - 1 with another velocity (cells at the shared edge see two moving
+    materials)."""
+    m = I.cavity_box(23, 19, 14)
+    m[:, -1, :] = I.WALL
+    m[1:-1, -1, :] = I.LID
+    m[:, :, -1] = 4
+    case = Case(1, m, 0, 0.58, walls={I.LID: (0.04, 0.0, 0.01), 4: (0.0, -0.02, 0.015)},
+                noise=I.population_noise(9, 19, m, 1e-5))
+    _compare(oracle, case, 37, dtype, scheme)
+
+
 def test_tgv3d_f64_and_f32(oracle, olb):
     case = tgv3d_case(24)
     _compare(oracle, case, 40, "f64", "pull")
