@@ -91,6 +91,18 @@ def test_moving_walls_beyond_the_plane_form(oracle, olb, dtype, scheme):
     _compare(oracle, case, 37, dtype, scheme)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("scheme", ["pull", "aa"])
+def test_cavity_rows_of_one_tile(oracle, olb, dtype, scheme):
+    """nx = 64: a row is exactly one tile of the paired kernel, and with walls on
+    both x faces each warp holds one pair of a wall cell and a fluid cell.  The rows
+    (21 x 13) do not fill the last block.  FP16 is held to its storage bound
+    (shifted values carry 11 significant bits)."""
+    case = cavity_case(64, 21, 13, lid=0.08)
+    _compare(oracle, case, 40, dtype, scheme, tol=1e-5 if dtype == "f32" else 2e-3)
+    _compare(oracle, case, 41, dtype, scheme, tol=1e-5 if dtype == "f32" else 2e-3)
+
+
 def test_tgv3d_f64_and_f32(oracle, olb):
     case = tgv3d_case(24)
     _compare(oracle, case, 40, "f64", "pull")
