@@ -134,11 +134,21 @@ typedef struct {
   const double* gamma;     // per-cell porosity in [0,1] or NULL (gamma = 1)
 } olb_oracle_lattice;
 
-// Objective: mean of u[component] over fluid cells whose coordinate along
-// plane_axis equals plane_index (discrete plane mode of the flux functors,
-// section "Discrete Flux Functor").
+// Objective of the adjoint, evaluated on the state after the last step.
+//   kind 0: mean of u[component] over the fluid cells whose coordinate along
+//           plane_axis equals plane_index (discrete plane mode of the flux functors,
+//           section "Discrete Flux Functor");
+//   kind 1: velocity misfit J = 1/2 sum over the fluid cells x of the region of
+//           |u(x) - u*(x)|^2, the objective 1/2 int |u - u*|^2 dx of the guide's
+//           optimisation examples (domainIdentification3d, testFlowOpti3d) with
+//           dx = 1 in lattice units; u_target = u* as [3][cells], region = per cell
+//           flag (nonzero: in the region; NULL: every fluid cell).  The sum runs over
+//           the d components of the lattice.
 typedef struct {
   int32_t plane_axis, plane_index, component;
+  int32_t kind;
+  const double* u_target;
+  const uint8_t* region;
 } olb_oracle_objective;
 
 }  // extern "C"
@@ -307,7 +317,14 @@ struct Sum {
 
 template <class T>
 bool objective_cells(const Geo& g, const olb_oracle_objective* obj, std::vector<int64_t>& cells) {
-  if (!obj || obj->plane_axis < 0 || obj->plane_axis > 2 || obj->component < 0 ||
+  if (!obj) return false;
+  if (obj->kind == 1) {
+    if (!obj->u_target) return false;
+    for (int64_t c = 0; c < g.n; ++c)
+      if (g.mat[c] == 1 && (!obj->region || obj->region[c] != 0)) cells.push_back(c);
+    return !cells.empty();
+  }
+  if (obj->kind != 0 || obj->plane_axis < 0 || obj->plane_axis > 2 || obj->component < 0 ||
       obj->component > 2)
     return false;
   int e[3] = {g.nx, g.ny, g.nz};
@@ -323,7 +340,8 @@ bool objective_cells(const Geo& g, const olb_oracle_objective* obj, std::vector<
 }
 
 template <class T>
-T loss_of(const olb_oracle_lattice* L, const T* f, const std::vector<int64_t>& cells, int comp) {
+T loss_of(const olb_oracle_lattice* L, const T* f, const std::vector<int64_t>& cells,
+          const olb_oracle_objective* obj) {
   Geo g(L);
   const Desc& D = *g.D;
   T acc = T(0.0);
@@ -331,9 +349,16 @@ T loss_of(const olb_oracle_lattice* L, const T* f, const std::vector<int64_t>& c
     T fc[19], rho, j[3], u[3];
     for (int i = 0; i < D.q; ++i) fc[i] = f[i * g.n + c];
     moments(D, fc, L->force, rho, j, u);
-    acc += u[comp];
+    if (obj->kind == 1) {
+      for (int a = 0; a < D.d; ++a) {
+        T e = u[a] - T(obj->u_target[a * g.n + c]);
+        acc += T(0.5) * e * e;
+      }
+    } else {
+      acc += u[obj->component];
+    }
   }
-  return acc / double(cells.size());
+  return obj->kind == 1 ? acc : acc / double(cells.size());
 }
 
 // Jacobian of one collision, J[k][i] = d f*_k / d f_i, plus d f*/d gamma and
@@ -582,7 +607,7 @@ int olb_oracle_loss(const olb_oracle_lattice* L, const double* f,
   Geo g(L);
   std::vector<int64_t> cells;
   if (!objective_cells<double>(g, obj, cells)) return -1;
-  *loss = loss_of<double>(L, f, cells, obj->component);
+  *loss = loss_of<double>(L, f, cells, obj);
   return 0;
 }
 
@@ -603,7 +628,7 @@ int olb_oracle_tangent(const olb_oracle_lattice* L, const double* f0, int64_t ns
   // omega = 1/tau, d omega = -d tau / tau^2
   Dual omega = Dual(1.0, 0.0) / Dual(L->tau, dtau_dir);
   step_field<Dual>(L, f.data(), gam.data(), omega, nsteps);
-  Dual Lv = loss_of<Dual>(L, f.data(), cells, obj->component);
+  Dual Lv = loss_of<Dual>(L, f.data(), cells, obj);
   *loss = Lv.v;
   *dloss = Lv.d;
   return 0;
@@ -668,15 +693,25 @@ int olb_oracle_adjoint(const olb_oracle_lattice* L, const double* f0, int64_t ns
     step_field<double>(L, states[s + 1].data(), L->gamma, 1.0 / L->tau, 1);
   }
   const std::vector<double>& fN = states[nsteps];
-  *loss = loss_of<double>(L, fN.data(), cells, obj->component);
-  // Seed: d/df_i of mean u_a = (1/M) (c_ia - u_a) / rho.
+  *loss = loss_of<double>(L, fN.data(), cells, obj);
+  // Seed lam^N = dL/df^N, with d u_a / d f_i = (c_ia - u_a) / rho:
+  //   plane mean of u_a:  (1/M) (c_ia - u_a) / rho
+  //   velocity misfit:    sum_a (u_a - u*_a) (c_ia - u_a) / rho
   std::vector<double> lam(qn, 0.0), lams(qn), lamn(qn), direct(g.n);
-  int a = obj->component;
   for (int64_t c : cells) {
     double fc[19], r, j[3], u[3];
     for (int i = 0; i < D.q; ++i) fc[i] = fN[i * g.n + c];
     moments(D, fc, L->force, r, j, u);
-    for (int i = 0; i < D.q; ++i) lam[i * g.n + c] = (D.c[i][a] - u[a]) / r / double(cells.size());
+    for (int i = 0; i < D.q; ++i) {
+      double v = 0.0;
+      if (obj->kind == 1) {
+        for (int a = 0; a < D.d; ++a) v += (u[a] - obj->u_target[a * g.n + c]) * (D.c[i][a] - u[a]) / r;
+      } else {
+        const int a = obj->component;
+        v = (D.c[i][a] - u[a]) / r / double(cells.size());
+      }
+      lam[i * g.n + c] = v;
+    }
   }
   std::vector<double> gg(g.n, 0.0);
   double domega = 0.0;

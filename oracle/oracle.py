@@ -53,7 +53,31 @@ class _Lattice(ctypes.Structure):
 
 class _Objective(ctypes.Structure):
     _fields_ = [("plane_axis", ctypes.c_int32), ("plane_index", ctypes.c_int32),
-                ("component", ctypes.c_int32)]
+                ("component", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("u_target", ctypes.c_void_p), ("region", ctypes.c_void_p)]
+
+
+@dataclass
+class Misfit:
+    """Velocity-misfit objective J = 1/2 sum over the fluid cells of the region of
+    |u - u*|^2 (the guide's optimisation examples).  u_target: [3, nz, ny, nx] (or
+    [d, ...]); region: bool/uint8 [nz, ny, nx] or None (every fluid cell)."""
+    u_target: np.ndarray
+    region: Optional[np.ndarray] = None
+
+
+def _objective(objective, shape):
+    """ctypes objective and the arrays it points into (kept alive by the caller)."""
+    if isinstance(objective, Misfit):
+        n = int(np.prod(shape))
+        ut = np.zeros((3, n))
+        src = np.asarray(objective.u_target, np.float64).reshape(-1, n)
+        ut[:src.shape[0]] = src
+        reg = None if objective.region is None else np.ascontiguousarray(
+            np.asarray(objective.region).reshape(n) != 0, np.uint8)
+        obj = _Objective(0, 0, 0, 1, ut.ctypes.data, None if reg is None else reg.ctypes.data)
+        return obj, (ut, reg)
+    return _Objective(*objective), ()
 
 
 _lib = None
@@ -212,14 +236,14 @@ class Lattice:
 
     def loss(self, f: np.ndarray, objective) -> float:
         out = ctypes.c_double()
-        obj = _Objective(*objective)
+        obj, keep = _objective(objective, self.shape)
         _check(lib().olb_oracle_loss(ctypes.byref(self._c()), _p(self._f(f)), ctypes.byref(obj),
                                      ctypes.byref(out)), "loss")
         return out.value
 
     def tangent(self, f0: np.ndarray, n: int, objective, dgamma=None, dtau: float = 0.0):
         loss, dl = ctypes.c_double(), ctypes.c_double()
-        obj = _Objective(*objective)
+        obj, keep = _objective(objective, self.shape)
         dg = None if dgamma is None else np.ascontiguousarray(dgamma, np.float64)
         _check(lib().olb_oracle_tangent(ctypes.byref(self._c()), _p(self._f(f0)), int(n),
                                         ctypes.byref(obj), _p(dg), float(dtau),
@@ -255,7 +279,7 @@ class Lattice:
         loss, dtau = ctypes.c_double(), ctypes.c_double()
         dg = np.zeros(self.shape)
         lam0 = self.zeros() if want_lambda0 else None
-        obj = _Objective(*objective)
+        obj, keep = _objective(objective, self.shape)
         _check(lib().olb_oracle_adjoint(ctypes.byref(self._c()), _p(self._f(f0)), int(n),
                                         ctypes.byref(obj), ctypes.byref(loss), _p(dg),
                                         ctypes.byref(dtau), _p(lam0)), "adjoint")

@@ -130,3 +130,128 @@ def test_adjoint_rejects_empty_objective_plane(oracle):
     lat, f0 = _porous_channel(oracle, 0, (1, 6, 6))
     with pytest.raises(ValueError):
         lat.adjoint(f0, 3, (1, 0, 0))  # plane y = 0 is all wall
+
+
+# ---------------------------------------------------------------------------------
+# Velocity-misfit objective J = 1/2 sum_region |u - u*|^2 (the guide's optimisation
+# examples domainIdentification3d and testFlowOpti3d, with dx = 1).
+# ---------------------------------------------------------------------------------
+def _misfit(oracle, lat, f0, n, seed=5):
+    """A target field u* (the final velocity of a run with another porosity, plus a
+    smooth offset) and a region (a box of the interior)."""
+    nz, ny, nx = lat.shape
+    g_alt = np.clip(lat.gamma * (0.8 + 0.4 * I.uniform(seed, lat.shape)), 0.0, 1.0)
+    saved = lat.gamma
+    lat.gamma = g_alt
+    f = f0.copy()
+    lat.step(f, n)
+    _, u_ref = lat.moments(f)
+    lat.gamma = saved
+    u_t = u_ref + 1e-3 * (I.uniform(seed + 1, u_ref.shape) - 0.5)
+    region = np.zeros(lat.shape, bool)
+    region[:, 1:ny - 1, nx // 4: nx - 1] = True
+    return oracle.Misfit(u_t, region)
+
+
+def test_misfit_loss_is_half_the_squared_velocity_error(oracle):
+    lat, f0 = _porous_channel(oracle, 1, (4, 6, 8))
+    f = f0.copy()
+    lat.step(f, 7)
+    obj = _misfit(oracle, lat, f0, 7)
+    _, u = lat.moments(f)
+    sel = obj.region & (lat.material == I.FLUID)
+    want = 0.5 * float(((u - obj.u_target) ** 2)[:, sel].sum())
+    assert abs(lat.loss(f, obj) - want) <= 1e-14 * want
+    # no region: every fluid cell; D2Q9 sums the two components only
+    lat2, f2 = _porous_channel(oracle, 0, (1, 6, 9))
+    _, u2 = lat2.moments(f2)
+    ut = np.zeros((3,) + lat2.shape)
+    ut[:2] = 0.01
+    ut[2] = 5.0  # ignored in 2D
+    fl = lat2.material == I.FLUID
+    want2 = 0.5 * float(((u2[:2] - 0.01) ** 2)[:, fl].sum())
+    assert abs(lat2.loss(f2, oracle.Misfit(ut)) - want2) <= 1e-14 * want2
+
+
+@pytest.mark.parametrize("d,moving", [(0, False), (1, False), (0, True), (1, True)])
+def test_misfit_adjoint_matches_tangent_linear(oracle, d, moving):
+    shape = (1, 8, 10) if d == 0 else (5, 6, 8)
+    lat, f0 = _porous_channel(oracle, d, shape, moving=moving)
+    n = 30
+    obj = _misfit(oracle, lat, f0, n)
+    loss, dg, dtau = lat.adjoint(f0, n, obj)
+    assert loss > 0
+    fl = lat.material == I.FLUID
+    for k, seed in enumerate((94, 95, 96)):
+        v = np.where(fl, I.uniform(seed, shape) - 0.5, 0.0)
+        s = 0.7 if k == 1 else 0.0
+        loss_t, dl = lat.tangent(f0, n, obj, dgamma=v, dtau=s)
+        assert loss_t == loss
+        pred = float((dg * v).sum() + dtau * s)
+        assert abs(pred - dl) <= 1e-11 * abs(dl), (pred, dl)
+
+
+def test_misfit_adjoint_matches_central_differences(oracle):
+    shape = (4, 6, 8)
+    lat, f0 = _porous_channel(oracle, 1, shape)
+    n = 25
+    obj = _misfit(oracle, lat, f0, n)
+    loss, dg, dtau = lat.adjoint(f0, n, obj)
+    cells = I.random_fluid_cells(4, lat.material, 6)
+    h = 1e-5
+    base_gamma = lat.gamma.copy()
+    for c in cells:
+        vals = []
+        for sgn in (1, -1):
+            g = base_gamma.copy()
+            g.reshape(-1)[c] += sgn * h
+            lat.gamma = g
+            f = f0.copy()
+            lat.step(f, n)
+            vals.append(lat.loss(f, obj))
+        lat.gamma = base_gamma
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - dg.reshape(-1)[c]) <= 1e-6 * abs(fd) + 1e-16
+    ht = 1e-6
+    vals = []
+    for sgn in (1, -1):
+        lat.tau = 0.8 + sgn * ht
+        f = f0.copy()
+        lat.step(f, n)
+        vals.append(lat.loss(f, obj))
+    lat.tau = 0.8
+    fd = (vals[0] - vals[1]) / (2 * ht)
+    assert abs(fd - dtau) <= 1e-6 * abs(fd)
+
+
+def test_misfit_gradient_vanishes_at_the_reference_and_descends_near_it(oracle):
+    """With u* the velocity of the current porosity the misfit is 0 and so is its
+    gradient; moving the porosity away and then a small step against the gradient
+    lowers the misfit (the steepest-descent step of the guide's optimisers)."""
+    shape = (4, 6, 8)
+    lat, f0 = _porous_channel(oracle, 1, shape)
+    n = 20
+    f = f0.copy()
+    lat.step(f, n)
+    _, u_ref = lat.moments(f)
+    obj = oracle.Misfit(u_ref)
+    loss, dg, dtau = lat.adjoint(f0, n, obj)
+    assert loss == 0.0 and not dg.any() and dtau == 0.0
+    g_true = lat.gamma.copy()
+    fl = lat.material == I.FLUID
+    lat.gamma = np.where(fl, np.clip(g_true - 0.2 * I.uniform(7, shape), 0.0, 1.0), g_true)
+    loss1, dg1, _ = lat.adjoint(f0, n, obj)
+    assert loss1 > 0
+    step = 0.1 * loss1 / float((dg1 ** 2).sum())
+    lat.gamma = lat.gamma - step * dg1
+    f = f0.copy()
+    lat.step(f, n)
+    assert lat.loss(f, obj) < loss1 * (1 - 0.05)
+
+
+def test_misfit_rejects_an_empty_region(oracle):
+    lat, f0 = _porous_channel(oracle, 0, (1, 6, 6))
+    region = np.zeros(lat.shape, bool)
+    region[:, 0, :] = True  # wall row only
+    with pytest.raises(ValueError):
+        lat.adjoint(f0, 3, oracle.Misfit(np.zeros((3,) + lat.shape), region))
