@@ -194,6 +194,25 @@ int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
                     const olb_objective* obj, double* loss, double* dL_dgamma,
                     double* dL_dtau);
 
+/* As olb_adjoint_run, for the velocity misfit
+ *     J = 1/2 sum over the fluid cells x of the region of |u(x) - u*(x)|^2
+ * on the final state: the objective 1/2 int |u - u*|^2 dx of the guide's
+ * optimisation examples (section "optimization": domainIdentification3d, where a
+ * porosity field is identified from a reference flow, and testFlowOpti3d), with
+ * dx = 1 in lattice units.  u = (j + F/2)/rho as in olb_moments; the sum runs over
+ * the lattice's d velocity components.
+ *   u_target  double [3][cells] (layout of olb_moments' u; the z row is ignored for
+ *             D2Q9), host or device memory, read during the call
+ *   region    uint8 [cells], nonzero = in the region, host or device memory, or
+ *             NULL (every fluid cell)
+ * Outputs as olb_adjoint_run: loss = J, dL_dgamma = dJ/dgamma (double [cells],
+ * device or host), dL_dtau = dJ/dtau.
+ * Errors: OLB_ERR_ARG (n_steps < 1, K < 1, NULL u_target, region without fluid
+ *         cells), OLB_ERR_OOM. */
+int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
+                           const double* u_target, const uint8_t* region, double* loss,
+                           double* dL_dgamma, double* dL_dtau);
+
 /* Block the host until all work queued on the handle's stream has finished;
  * reports asynchronous CUDA errors as OLB_ERR_CUDA. */
 int olb_synchronize(olb_handle h);

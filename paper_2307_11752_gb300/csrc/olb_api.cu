@@ -491,6 +491,95 @@ int upload_wall(olb_handle h) {
   return OLB_OK;
 }
 
+// Forward sweep with checkpoints, objective seed, reverse sweep with segment
+// recompute (olb_adjoint_run and olb_adjoint_run_misfit).  `seed` launches the
+// kernel that writes lam^N = dL/df^N and the objective's partial sums (row 0);
+// loss = loss_scale * (sum of row 0).
+template <class Seed>
+int adjoint_sweep(olb_handle h, int64_t n_steps, int64_t K, Seed&& seed, double loss_scale, double* loss,
+                  double* dL_dgamma, double* dL_dtau) {
+  int rc;
+  if (K > n_steps) K = n_steps;
+  const int64_t nseg = (n_steps + K - 1) / K;
+  const size_t sb = h->state_bytes();
+  const size_t lb = (size_t)h->q * h->pitch * h->kt->lambda_elem;
+  const int64_t rows = h->cell_rows();
+
+  // buffers: checkpoints, segment slots 1..K-1, two adjoint fields, gradients
+  std::vector<DevBuf> ckpt(nseg), seg(K);
+  std::vector<int> ckpt_repr(nseg);
+  DevBuf lam[2], dg, part;
+  for (auto& b : ckpt)
+    if ((rc = b.reserve(sb))) return rc;
+  for (int64_t k = 1; k < K; ++k)
+    if ((rc = seg[k].reserve(sb))) return rc;
+  if ((rc = lam[0].reserve(lb)) || (rc = lam[1].reserve(lb)) || (rc = dg.reserve((size_t)h->ncell * 8)) ||
+      (rc = part.reserve((size_t)rows * 8 * sizeof(double))) || (rc = ensure_partials(h, h->grid_blocks())))
+    return rc;
+  if (h->repr == AA_ODD && (rc = materialize(h))) return rc;
+
+  // forward sweep with checkpoints (pull pattern)
+  const int saved_scheme = h->scheme;
+  h->scheme = OLB_PULL;
+  for (int64_t s = 0; s < nseg; ++s) {
+    OLB_CUDA(cudaMemcpyAsync(ckpt[s].p, h->buf[h->cur].p, sb, cudaMemcpyDeviceToDevice, h->stream), "checkpoint");
+    ckpt_repr[s] = h->repr;
+    const int64_t ks = std::min<int64_t>(K, n_steps - s * K);
+    for (int64_t k = 0; k < ks; ++k)
+      if ((rc = step_once(h, false, nullptr))) {
+        h->scheme = saved_scheme;
+        return rc;
+      }
+  }
+  h->scheme = saved_scheme;
+
+  // objective and seed lam^N
+  HostParams p = h->params();
+  const KernelTable* kt = h->kt;
+  double* partials = static_cast<double*>(h->partials.p);
+  if ((rc = launched(h, seed(p, h->buf[h->cur].p, lam[0].p, partials), "loss"))) return rc;
+  if ((rc = launched(h, reduce_partials(partials, rows, static_cast<double*>(h->out8.p), h->stream), "loss reduce")))
+    return rc;
+  double lsum[8];
+  OLB_CUDA(cudaMemcpyAsync(lsum, h->out8.p, sizeof(lsum), cudaMemcpyDeviceToHost, h->stream), "loss copy");
+  OLB_CUDA(cudaMemsetAsync(dg.p, 0, (size_t)h->ncell * 8, h->stream), "gradient clear");
+  OLB_CUDA(cudaMemsetAsync(part.p, 0, (size_t)rows * 8 * sizeof(double), h->stream), "partials clear");
+
+  // reverse sweep: recompute each segment, then step the adjoint back through it
+  int li = 0;
+  for (int64_t s = nseg - 1; s >= 0; --s) {
+    const int64_t ks = std::min<int64_t>(K, n_steps - s * K);
+    std::vector<const void*> slot(ks);
+    std::vector<int> srepr(ks);
+    slot[0] = ckpt[s].p;
+    srepr[0] = ckpt_repr[s];
+    for (int64_t k = 1; k < ks; ++k) {
+      const int g = srepr[k - 1] == PRE ? G_OWN : G_PULL;
+      if ((rc = launched(h, kt->step(p, g, S_OWN, false, slot[k - 1], seg[k].p, nullptr), "recompute"))) return rc;
+      slot[k] = seg[k].p;
+      srepr[k] = POST;
+    }
+    for (int64_t k = ks - 1; k >= 0; --k) {
+      const int g = srepr[k] == PRE ? G_OWN : G_PULL;
+      if ((rc = launched(h, kt->adjoint(p, g, slot[k], lam[li].p, lam[1 - li].p, static_cast<double*>(dg.p),
+                                        static_cast<double*>(part.p)), "adjoint")))
+        return rc;
+      li = 1 - li;
+    }
+  }
+  if ((rc = launched(h, reduce_partials(static_cast<double*>(part.p), rows, static_cast<double*>(h->out8.p), h->stream), "gradient reduce")))
+    return rc;
+  double gsum[8];
+  OLB_CUDA(cudaMemcpyAsync(gsum, h->out8.p, sizeof(gsum), cudaMemcpyDeviceToHost, h->stream), "gradient copy");
+  if (dL_dgamma) {
+    OLB_CUDA(cudaMemcpyAsync(dL_dgamma, dg.p, (size_t)h->ncell * 8, cudaMemcpyDefault, h->stream), "gradient out");
+  }
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "adjoint sync");
+  if (loss) *loss = lsum[0] * loss_scale;
+  if (dL_dtau) *dL_dtau = -gsum[0] / (h->tau * h->tau);
+  return OLB_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------
@@ -883,87 +972,42 @@ int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t K, const olb_objectiv
           ++count;
       }
   if (count == 0) return fail(OLB_ERR_ARG, "objective plane holds no fluid cell");
-  if (K > n_steps) K = n_steps;
-  const int64_t nseg = (n_steps + K - 1) / K;
-  const size_t sb = h->state_bytes();
-  const size_t lb = (size_t)h->q * h->pitch * h->kt->lambda_elem;
-  const int64_t rows = h->cell_rows();
+  const double inv_count = 1.0 / (double)count;
+  auto seed = [&](const HostParams& p, const void* state, void* lam0, double* partials) {
+    return h->kt->loss_seed(p, gather_of(h->repr), state, obj->plane_axis, obj->plane_index, obj->component,
+                            inv_count, lam0, partials);
+  };
+  return adjoint_sweep(h, n_steps, K, seed, inv_count, loss, dL_dgamma, dL_dtau);
+}
 
-  // buffers: checkpoints, segment slots 1..K-1, two adjoint fields, gradients
-  std::vector<DevBuf> ckpt(nseg), seg(K);
-  std::vector<int> ckpt_repr(nseg);
-  DevBuf lam[2], dg, part;
-  for (auto& b : ckpt)
-    if ((rc = b.reserve(sb))) return rc;
-  for (int64_t k = 1; k < K; ++k)
-    if ((rc = seg[k].reserve(sb))) return rc;
-  if ((rc = lam[0].reserve(lb)) || (rc = lam[1].reserve(lb)) || (rc = dg.reserve((size_t)h->ncell * 8)) ||
-      (rc = part.reserve((size_t)rows * 8 * sizeof(double))) || (rc = ensure_partials(h, h->grid_blocks())))
-    return rc;
-  if (h->repr == AA_ODD && (rc = materialize(h))) return rc;
-
-  // forward sweep with checkpoints (pull pattern)
-  const int saved_scheme = h->scheme;
-  h->scheme = OLB_PULL;
-  for (int64_t s = 0; s < nseg; ++s) {
-    OLB_CUDA(cudaMemcpyAsync(ckpt[s].p, h->buf[h->cur].p, sb, cudaMemcpyDeviceToDevice, h->stream), "checkpoint");
-    ckpt_repr[s] = h->repr;
-    const int64_t ks = std::min<int64_t>(K, n_steps - s * K);
-    for (int64_t k = 0; k < ks; ++k)
-      if ((rc = step_once(h, false, nullptr))) {
-        h->scheme = saved_scheme;
-        return rc;
-      }
+int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t K, const double* u_target,
+                           const uint8_t* region, double* loss, double* dL_dgamma, double* dL_dtau) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (n_steps < 1 || K < 1) return fail(OLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+  if (!u_target) return fail(OLB_ERR_ARG, "null target velocity");
+  const size_t n = (size_t)h->ncell;
+  // the region on the host, to count its fluid cells before any work is queued
+  std::vector<uint8_t> reg_host;
+  if (region) {
+    reg_host.resize(n);
+    OLB_CUDA(cudaMemcpyAsync(reg_host.data(), region, n, cudaMemcpyDefault, h->stream), "region copy");
+    OLB_CUDA(cudaStreamSynchronize(h->stream), "region sync");
   }
-  h->scheme = saved_scheme;
-
-  // objective and seed lam^N
-  HostParams p = h->params();
-  const KernelTable* kt = h->kt;
-  double* partials = static_cast<double*>(h->partials.p);
-  if ((rc = launched(h, kt->loss_seed(p, gather_of(h->repr), h->buf[h->cur].p, obj->plane_axis, obj->plane_index,
-                                      obj->component, 1.0 / (double)count, lam[0].p, partials), "loss")))
-    return rc;
-  if ((rc = launched(h, reduce_partials(partials, rows, static_cast<double*>(h->out8.p), h->stream), "loss reduce")))
-    return rc;
-  double lsum[8];
-  OLB_CUDA(cudaMemcpyAsync(lsum, h->out8.p, sizeof(lsum), cudaMemcpyDeviceToHost, h->stream), "loss copy");
-  OLB_CUDA(cudaMemsetAsync(dg.p, 0, (size_t)h->ncell * 8, h->stream), "gradient clear");
-  OLB_CUDA(cudaMemsetAsync(part.p, 0, (size_t)rows * 8 * sizeof(double), h->stream), "partials clear");
-
-  // reverse sweep: recompute each segment, then step the adjoint back through it
-  int li = 0;
-  for (int64_t s = nseg - 1; s >= 0; --s) {
-    const int64_t ks = std::min<int64_t>(K, n_steps - s * K);
-    std::vector<const void*> slot(ks);
-    std::vector<int> srepr(ks);
-    slot[0] = ckpt[s].p;
-    srepr[0] = ckpt_repr[s];
-    for (int64_t k = 1; k < ks; ++k) {
-      const int g = srepr[k - 1] == PRE ? G_OWN : G_PULL;
-      if ((rc = launched(h, kt->step(p, g, S_OWN, false, slot[k - 1], seg[k].p, nullptr), "recompute"))) return rc;
-      slot[k] = seg[k].p;
-      srepr[k] = POST;
-    }
-    for (int64_t k = ks - 1; k >= 0; --k) {
-      const int g = srepr[k] == PRE ? G_OWN : G_PULL;
-      if ((rc = launched(h, kt->adjoint(p, g, slot[k], lam[li].p, lam[1 - li].p, static_cast<double*>(dg.p),
-                                        static_cast<double*>(part.p)), "adjoint")))
-        return rc;
-      li = 1 - li;
-    }
-  }
-  if ((rc = launched(h, reduce_partials(static_cast<double*>(part.p), rows, static_cast<double*>(h->out8.p), h->stream), "gradient reduce")))
-    return rc;
-  double gsum[8];
-  OLB_CUDA(cudaMemcpyAsync(gsum, h->out8.p, sizeof(gsum), cudaMemcpyDeviceToHost, h->stream), "gradient copy");
-  if (dL_dgamma) {
-    OLB_CUDA(cudaMemcpyAsync(dL_dgamma, dg.p, (size_t)h->ncell * 8, cudaMemcpyDefault, h->stream), "gradient out");
-  }
-  OLB_CUDA(cudaStreamSynchronize(h->stream), "adjoint sync");
-  if (loss) *loss = lsum[0] / (double)count;
-  if (dL_dtau) *dL_dtau = -gsum[0] / (h->tau * h->tau);
-  return OLB_OK;
+  int64_t count = 0;
+  for (size_t c = 0; c < n; ++c)
+    if (h->h_mat[c] == OLB_MAT_FLUID && (!region || reg_host[c] != 0)) ++count;
+  if (count == 0) return fail(OLB_ERR_ARG, "objective region holds no fluid cell");
+  DevBuf ut_tmp, reg_tmp;
+  const void* ut = nullptr;
+  const void* rg = nullptr;
+  if ((rc = input_view(h, u_target, 3 * n * sizeof(double), ut_tmp, &ut))) return rc;
+  if (region && (rc = input_view(h, region, n, reg_tmp, &rg))) return rc;
+  auto seed = [&](const HostParams& p, const void* state, void* lam0, double* partials) {
+    return h->kt->misfit_seed(p, gather_of(h->repr), state, static_cast<const double*>(ut),
+                              static_cast<const uint8_t*>(rg), lam0, partials);
+  };
+  return adjoint_sweep(h, n_steps, K, seed, 1.0, loss, dL_dgamma, dL_dtau);
 }
 
 }  // extern "C"

@@ -90,6 +90,8 @@ struct KernelTable {
                          void* lam_out, double* dgamma, double* partials);
   cudaError_t (*loss_seed)(const HostParams&, int gather, const void* src, int axis, int index,
                            int comp, double inv_count, void* lam, double* partials);
+  cudaError_t (*misfit_seed)(const HostParams&, int gather, const void* src, const double* u_target,
+                             const uint8_t* region, void* lam, double* partials);
 };
 
 // dtype: 0 f64, 1 f32, 2 f16 (shifted), 3 bf16 (shifted)

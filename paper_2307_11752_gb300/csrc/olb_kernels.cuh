@@ -958,6 +958,54 @@ __global__ void __launch_bounds__(256) k_loss_seed(Params<typename Store<S>::C> 
   block_reduce_row(sv, partials + 8 * block_linear(), false);
 }
 
+// Seed of the adjoint for the velocity misfit J = 1/2 sum over the fluid cells of
+// the region of |u - u*|^2 (the objective of the guide's optimisation examples,
+// section "optimization": domainIdentification3d, testFlowOpti3d), on the final
+// state: lam_i = dJ/df_i = sum_a (u_a - u*_a) (c_ia - u_a) / rho, zero elsewhere.
+// u_target is [d][cells] (FP64, canonical cell order), region a per-cell flag or
+// nullptr (every fluid cell).  Partial row k = 0: J, k = 1: cells counted.
+template <class L, class S, int G>
+__global__ void __launch_bounds__(256) k_misfit_seed(Params<typename Store<S>::C> p, const S* src,
+                                                     const double* u_target, const uint8_t* region,
+                                                     typename LambdaOf<S>::T* lam, double* partials) {
+  using C = typename Store<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const size_t N = (size_t)p.pitch;
+  C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
+  if (x < p.nx && y < p.ny) {
+    const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
+    const int cls = p.all_fluid ? 1 : p.cls[n.cell];
+    if (cls != 0 && (region == nullptr || region[n.cell] != 0)) {
+      C f[L::Q];
+      gather<L, S, G>(p, src, n, cls, f);
+      C drho, j[3];
+      moments<L>(f, drho, j);
+      const C rho = C(1) + drho;
+      const C inv = C(1) / rho;
+      C u[3], e[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        u[a] = (j[a] + p.half_force[a]) * inv;
+        e[a] = a < L::DIM ? u[a] - (C)u_target[(size_t)a * p.ncell + n.cell] : C(0);
+        sv[0] += C(0.5) * e[a] * e[a];
+      }
+      sv[1] = C(1);
+      // sum_a e_a (c_ia - u_a) / rho = (e . c_i - e . u) / rho
+      const C eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const C ec = L::c(i, 0) * e[0] + L::c(i, 1) * e[1] + L::c(i, 2) * e[2];
+        lam[i * N + n.cell] = (typename LambdaOf<S>::T)((ec - eu) * inv);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) lam[i * N + n.cell] = 0;
+    }
+  }
+  block_reduce_row(sv, partials + 8 * block_linear(), false);
+}
+
 }  // namespace olb
 
 #include "olb_pair.cuh"
@@ -1066,6 +1114,10 @@ struct Launch {
     OLB_BY_GATHER(k_loss_seed, static_cast<const S*>(src), axis, index, comp, inv_count,
                   static_cast<T*>(lam), partials);
   }
+  static cudaError_t misfit_seed(const HostParams& h, int gather, const void* src, const double* u_target,
+                                 const uint8_t* region, void* lam, double* partials) {
+    OLB_BY_GATHER(k_misfit_seed, static_cast<const S*>(src), u_target, region, static_cast<T*>(lam), partials);
+  }
   static cudaError_t adjoint(const HostParams& h, int gather, const void* state,
                              const void* lam_in, void* lam_out, double* dgamma,
                              double* partials) {
@@ -1094,7 +1146,7 @@ struct Launch {
   static const KernelTable* table() {
     static const KernelTable t = {L::Q,       sizeof(S), sizeof(T), &step,    &to_f64,
                                   &moments,   &stats,    &from_f64, &init_eq, &perturb,
-                                  &materialize, &adjoint, &loss_seed};
+                                  &materialize, &adjoint, &loss_seed, &misfit_seed};
     return &t;
   }
 };

@@ -53,6 +53,7 @@ SIGNATURES = {
     "olb_moments": [_P, _P, _P],
     "olb_diagnostics": [_P, _P],
     "olb_adjoint_run": [_P, _I64, _I64, _P, _P, _P, _P],
+    "olb_adjoint_run_misfit": [_P, _I64, _I64, _P, _P, _P, _P, _P],
     "olb_synchronize": [_P],
     "olb_counters": [_P, _P, _P],
     "olb_statistics_noalloc": [_I, _I, _I, _I, _P, _P, _P, _P, _P],
@@ -317,6 +318,27 @@ class Lattice:
               ctypes.byref(loss), p, ctypes.byref(dtau))
         return loss.value, dgamma, dtau.value
 
+    def adjoint_run_misfit(self, n_steps: int, checkpoint_every: int, u_target, region=None, dgamma=None):
+        """Velocity misfit J = 1/2 sum over the region's fluid cells of |u - u*|^2 after
+        ``n_steps`` steps: (J, dJ/dgamma as a CUDA float64 tensor [nz, ny, nx], dJ/dtau).
+        ``u_target``: float64 [3, nz, ny, nx] (CUDA tensor or host array); ``region``:
+        uint8 [nz, ny, nx] or None (every fluid cell)."""
+        import torch
+
+        if dgamma is None:
+            dgamma = torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device="cuda")
+        _check_array(dgamma, "float64", self.cells, "dgamma")
+        _check_array(u_target, "float64", 3 * self.cells, "u_target")
+        if region is not None:
+            _check_array(region, "uint8", self.cells, "region")
+        loss, dtau = ctypes.c_double(), ctypes.c_double()
+        pg, kg = _ptr(dgamma)
+        pu, ku = _ptr(u_target)
+        pr, kr = _ptr(region)
+        _call("olb_adjoint_run_misfit", self.handle, int(n_steps), int(checkpoint_every), pu, pr,
+              ctypes.byref(loss), pg, ctypes.byref(dtau))
+        return loss.value, dgamma, dtau.value
+
     def synchronize(self):
         _call("olb_synchronize", self.handle)
 
@@ -357,3 +379,35 @@ def plane_velocity_loss(lattice: Lattice, gamma, tau, f0, n_steps: int, checkpoi
             return grad * dg.view_as(gamma), grad_tau
 
     return _PlaneVelocityLoss.apply(gamma, tau)
+
+
+def velocity_misfit_loss(lattice: Lattice, gamma, tau, f0, n_steps: int, checkpoint_every: int,
+                         u_target, region=None):
+    """J = 1/2 sum over the fluid cells of ``region`` of |u - u*|^2 after ``n_steps``
+    steps from ``f0`` (the objective of the guide's domain identification), as a
+    differentiable function of ``gamma`` (float64 CUDA tensor [nz, ny, nx]) and
+    ``tau`` (0-d float64 tensor); backward returns the gradients of
+    ``olb_adjoint_run_misfit``.  Compose it with a projection gamma = p(alpha) and any
+    torch optimiser."""
+    import torch
+
+    class _VelocityMisfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, g, t):
+            lattice.set_bgk(float(t))
+            lattice.set_porosity(g.detach().contiguous())
+            lattice.set_populations(f0)
+            loss, dg, dtau = lattice.adjoint_run_misfit(n_steps, checkpoint_every, u_target, region)
+            ctx.save_for_backward(dg)
+            ctx.dtau = dtau
+            ctx.tau_meta = (t.dtype, t.device)
+            return torch.tensor(loss, dtype=torch.float64, device=g.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            (dg,) = ctx.saved_tensors
+            dtype, device = ctx.tau_meta
+            grad_tau = torch.tensor(float(grad) * ctx.dtau, dtype=dtype, device=device)
+            return grad * dg.view_as(gamma), grad_tau
+
+    return _VelocityMisfit.apply(gamma, tau)
