@@ -359,6 +359,78 @@ def experiment_adjoint384(torch, olb, fd_cells=4):
     return res
 
 
+def experiment_domain_id(torch, olb, dtype="f32", iterations=20):
+    """Domain identification at scale (the guide's domainIdentification3d): a cube
+    of porosity 0.05 (16^3 cells) in the forced channel 192x96x96 (periodic x, walls
+    on y and z, tau 0.8), 1500 steps from rest.  The reference velocity u* comes
+    from a forward run with the cube; the porosity of a 32^3 design box around it is
+    then identified from u* on the fluid cells outside the box (velocity misfit,
+    sigmoid projection, start 0.7, torch L-BFGS with strong Wolfe line search).
+    Every evaluation is one checkpointed adjoint run (K = 100)."""
+    from paper_2307_11752_gb300 import opti
+
+    nx, ny, nz, steps, K, tau = 192, 96, 96, 1500, 100, 0.8
+    m = I.channel(nx, ny, nz)
+    lat = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype=dtype, scheme="pull")
+    lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 1)
+    lat.set_bgk(tau)
+    lat.set_force((I.channel_force(ny, tau), 0, 0))
+    lat.init_equilibrium()
+    f0 = lat.get_populations().clone()
+    truth = torch.ones((nz, ny, nx), dtype=torch.float64, device="cuda")
+    cz, cy, cx = nz // 2, ny // 2, nx // 3
+    truth[cz - 8:cz + 8, cy - 8:cy + 8, cx - 8:cx + 8] = 0.05
+    lat.set_porosity(truth.reshape(-1).contiguous())
+    lat.step(steps)
+    _, u_ref = lat.moments()
+    fl = torch.from_numpy(m == I.FLUID).cuda()
+    design = torch.zeros_like(fl)
+    design[cz - 16:cz + 16, cy - 16:cy + 16, cx - 16:cx + 16] = True
+    design &= fl
+    region = (fl & ~design).to(torch.uint8)
+    tau_t = torch.tensor(tau, dtype=torch.float64)
+    times = []
+
+    def evaluate(gamma):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        J = olb.velocity_misfit_loss(lat, gamma, tau_t, f0, steps, K, u_ref, region)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+        return J
+
+    t0 = time.perf_counter()
+    res = opti.identify_porosity(evaluate, torch.ones_like(truth), design, 0.7, iterations=iterations)
+    wall = time.perf_counter() - t0
+    inside = truth < 0.5
+    core = torch.zeros_like(inside)
+    core[cz - 7:cz + 7, cy - 7:cy + 7, cx - 7:cx + 7] = True
+    shell = inside & ~core
+    g = res.gamma
+    fluid = int(fl.sum())
+    ev = float(np.median(times))
+    out = {
+        "workload": f"domain identification, channel {nx}x{ny}x{nz} ({dtype} storage), {steps} steps, K={K}, "
+                    f"cube 16^3 of porosity 0.05, design box 32^3 ({int(design.sum())} cells), "
+                    f"objective on {int(region.sum())} fluid cells outside the box",
+        "iterations": len(res.objective) - 1, "evaluations": res.evaluations, "seconds": round(wall, 2),
+        "seconds_per_evaluation": round(ev, 3),
+        "MLUPS_per_evaluation": round(fluid * steps / ev / 1e6, 1),
+        "objective_first": res.objective[0], "objective_last": res.objective[-1],
+        "objective_ratio": res.objective[-1] / res.objective[0],
+        "objective": res.objective,
+        "gamma_mean_in_cube": float(g[inside].mean()),
+        "gamma_mean_cube_shell": float(g[shell].mean()),
+        "gamma_mean_cube_core": float(g[core].mean()),
+        "gamma_mean_design_outside_cube": float(g[design & ~inside].mean()),
+        "gamma_min_design_outside_cube": float(g[design & ~inside].min()),
+        "design_cells_below_half": int((g[design] < 0.5).sum()),
+        "cube_shell_cells_below_half": int((g[shell] < 0.5).sum()), "cube_shell_cells": int(shell.sum()),
+    }
+    lat.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -503,16 +575,17 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--experiment", choices=["adjoint384"], default=None,
+    ap.add_argument("--experiment", choices=["adjoint384", "domain_id"], default=None,
                     help="run a named experiment instead of the benchmark and print its JSON")
     args = ap.parse_args()
-    if args.experiment == "adjoint384":
+    if args.experiment is not None:
         import torch
 
         from paper_2307_11752_gb300 import build, olb
         build.build()
         olb.load()
-        print(json.dumps(experiment_adjoint384(torch, olb)), flush=True)
+        run = {"adjoint384": experiment_adjoint384, "domain_id": experiment_domain_id}[args.experiment]
+        print(json.dumps(run(torch, olb)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
