@@ -126,12 +126,13 @@ typedef struct {
   int32_t descriptor;      // 0 = D2Q9, 1 = D3Q19
   int32_t nx, ny, nz;      // nz = 1 for D2Q9
   uint32_t periodic;       // bit 0: x, bit 1: y, bit 2: z
-  int32_t reserved;
+  int32_t collision;       // 0 = BGK, 1 = TRT (two relaxation times, magic parameter below)
   const uint8_t* material; // nx*ny*nz, x fastest; 1 = fluid, 0 void, 2 wall, >= 3 moving wall
   const double* wall_u;    // [256][3] wall velocity per material number (rows 0..2 unused)
   double tau;              // BGK relaxation time, omega = 1/tau
   double force[3];         // uniform body force density F (Guo)
   const double* gamma;     // per-cell porosity in [0,1] or NULL (gamma = 1)
+  double magic;            // TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2), omega+ = 1/tau
 } olb_oracle_lattice;
 
 // Objective of the adjoint, evaluated on the state after the last step.
@@ -186,6 +187,7 @@ bool valid(const olb_oracle_lattice* L) {
   if (L->nx < 1 || L->ny < 1 || L->nz < 1) return false;
   if (L->descriptor == 0 && L->nz != 1) return false;
   if (!(L->tau > 0.5)) return false;
+  if (L->collision != 0 && !(L->collision == 1 && L->magic > 0.0)) return false;
   return true;
 }
 
@@ -230,6 +232,43 @@ void collide_cell(const Desc& D, const T* f, T gamma, T omega, const double F[3]
   }
 }
 
+// One TRT collision (collision::TRT of the dynamics tuples, section "Dynamics"; the
+// guide names the operator without printing it -- read as the two-relaxation-time
+// operator of Ginzburg): with the even and odd parts g+-_i = (g_i +- g_opp(i))/2 of
+// f, f^eq and the Guo source S,
+//   f*_i = f_i - omega+ (f+_i - feq+_i) - omega- (f-_i - feq-_i)
+//              + (1 - omega+/2) S+_i + (1 - omega-/2) S-_i,
+// omega+ = 1/tau sets the viscosity, omega- follows from the magic parameter
+// Lambda = (1/omega+ - 1/2)(1/omega- - 1/2).  omega- = omega+ is BGK.
+template <class T>
+void collide_cell_trt(const Desc& D, const T* f, T gamma, T omega_p, T omega_m, const double F[3], T* fs) {
+  T rho, j[3], u[3];
+  moments(D, f, F, rho, j, u);
+  T up[3] = {gamma * u[0], gamma * u[1], gamma * u[2]};
+  T feq[19], S[19];
+  equilibrium(D, rho, up, feq);
+  T uF = up[0] * F[0] + up[1] * F[1] + up[2] * F[2];
+  for (int i = 0; i < D.q; ++i) {
+    double cF = D.c[i][0] * F[0] + D.c[i][1] * F[1] + D.c[i][2] * F[2];
+    T cu = D.c[i][0] * up[0] + D.c[i][1] * up[1] + D.c[i][2] * up[2];
+    S[i] = D.w[i] * ((T(cF) - uF) / D.cs2 + cu * cF / (D.cs2 * D.cs2));
+  }
+  for (int i = 0; i < D.q; ++i) {
+    const int o = D.opp[i];
+    T fp = T(0.5) * (f[i] + f[o]), fm = T(0.5) * (f[i] - f[o]);
+    T ep = T(0.5) * (feq[i] + feq[o]), em = T(0.5) * (feq[i] - feq[o]);
+    T sp = T(0.5) * (S[i] + S[o]), sm = T(0.5) * (S[i] - S[o]);
+    fs[i] = f[i] - omega_p * (fp - ep) - omega_m * (fm - em) + (T(1.0) - T(0.5) * omega_p) * sp +
+            (T(1.0) - T(0.5) * omega_m) * sm;
+  }
+}
+
+// omega- of the TRT operator from omega+ and the magic parameter.
+template <class T>
+T omega_minus(T omega_p, double magic) {
+  return T(1.0) / (T(magic) / (T(1.0) / omega_p - T(0.5)) + T(0.5));
+}
+
 template <class T>
 T gamma_at(const olb_oracle_lattice* L, const T* gamma, int64_t c) {
   if (gamma) return gamma[c];
@@ -242,12 +281,17 @@ template <class T>
 void collide_field(const olb_oracle_lattice* L, const T* f, const T* gamma, T omega, T* fs) {
   Geo g(L);
   const Desc& D = *g.D;
+  const bool trt = L->collision == 1;
+  const T om_m = trt ? omega_minus(omega, L->magic) : omega;
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < g.n; ++c) {
     T fc[19], fsc[19];
     for (int i = 0; i < D.q; ++i) fc[i] = f[i * g.n + c];
     if (g.mat[c] == 1) {
-      collide_cell(D, fc, gamma_at(L, gamma, c), omega, L->force, fsc);
+      if (trt)
+        collide_cell_trt(D, fc, gamma_at(L, gamma, c), omega, om_m, L->force, fsc);
+      else
+        collide_cell(D, fc, gamma_at(L, gamma, c), omega, L->force, fsc);
     } else {
       for (int i = 0; i < D.q; ++i) fsc[i] = fc[i];
     }
@@ -512,6 +556,15 @@ int olb_oracle_collide_cell(int d, const double* f, double gamma, double tau,
   return 0;
 }
 
+// Single-cell TRT collision with magic parameter Lambda.
+int olb_oracle_collide_cell_trt(int d, const double* f, double gamma, double tau, double magic,
+                                const double* F, double* fs) {
+  const Desc* D = descriptor(d);
+  if (!D || !(tau > 0.5) || !(magic > 0.0)) return -1;
+  collide_cell_trt(*D, f, gamma, 1.0 / tau, omega_minus(1.0 / tau, magic), F, fs);
+  return 0;
+}
+
 // f = f^eq(rho, u) on every cell (section "Define Initial Conditions", iniEquilibrium).
 // rho: n, u: [3][n] (x, y, z components), f: [q][n].
 int olb_oracle_init_equilibrium(const olb_oracle_lattice* L, const double* rho,
@@ -654,7 +707,7 @@ int olb_oracle_collide_tangent(const olb_oracle_lattice* L, const double* f, con
 //   lam = (dC/df)^T lams;  dgamma += (dC/dgamma)^T lams;  dtau += (dC/dtau)^T lams
 int olb_oracle_collide_adjoint(const olb_oracle_lattice* L, const double* f,
                                const double* lams, double* lam, double* dgamma, double* dtau) {
-  if (!valid(L)) return -1;
+  if (!valid(L) || L->collision != 0) return -1;  // the Jacobian is written out for BGK
   double domega = 0.0;
   collide_transpose(L, f, lams, lam, dgamma, &domega);
   if (dtau) *dtau += -domega / (L->tau * L->tau);
@@ -680,7 +733,7 @@ int olb_oracle_stream_adjoint(const olb_oracle_lattice* L, const double* lam, do
 int olb_oracle_adjoint(const olb_oracle_lattice* L, const double* f0, int64_t nsteps,
                        const olb_oracle_objective* obj, double* loss, double* dgamma,
                        double* dtau, double* lambda0) {
-  if (!valid(L) || nsteps < 0) return -1;
+  if (!valid(L) || nsteps < 0 || L->collision != 0) return -1;  // BGK Jacobian only
   Geo g(L);
   const Desc& D = *g.D;
   std::vector<int64_t> cells;

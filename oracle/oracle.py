@@ -45,10 +45,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
 class _Lattice(ctypes.Structure):
     _fields_ = [("descriptor", ctypes.c_int32), ("nx", ctypes.c_int32),
                 ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("periodic", ctypes.c_uint32), ("reserved", ctypes.c_int32),
+                ("periodic", ctypes.c_uint32), ("collision", ctypes.c_int32),
                 ("material", ctypes.c_void_p), ("wall_u", ctypes.c_void_p),
                 ("tau", ctypes.c_double), ("force", ctypes.c_double * 3),
-                ("gamma", ctypes.c_void_p)]
+                ("gamma", ctypes.c_void_p), ("magic", ctypes.c_double)]
 
 
 class _Objective(ctypes.Structure):
@@ -93,6 +93,7 @@ def lib():
             "olb_oracle_descriptor": [ctypes.c_int, P, P, P, P, P, P],
             "olb_oracle_equilibrium": [ctypes.c_int, D, P, P],
             "olb_oracle_collide_cell": [ctypes.c_int, P, D, D, P, P],
+            "olb_oracle_collide_cell_trt": [ctypes.c_int, P, D, D, D, P, P],
             "olb_oracle_init_equilibrium": [P, P, P, P],
             "olb_oracle_collide": [P, P, P],
             "olb_oracle_stream": [P, P, P, P],
@@ -153,9 +154,24 @@ def collide_cell(d: int, f: np.ndarray, tau: float, gamma: float = 1.0, F=(0, 0,
     return out
 
 
+def collide_cell_trt(d: int, f: np.ndarray, tau: float, magic: float, gamma: float = 1.0,
+                     F=(0, 0, 0)) -> np.ndarray:
+    f = np.ascontiguousarray(f, np.float64)
+    FF = np.zeros(3)
+    FF[:len(F)] = F
+    out = np.zeros_like(f)
+    _check(lib().olb_oracle_collide_cell_trt(d, _p(f), float(gamma), float(tau), float(magic), _p(FF),
+                                             _p(out)), "collide_cell_trt")
+    return out
+
+
+BGK, TRT = 0, 1
+
+
 @dataclass
 class Lattice:
-    """A lattice description for the oracle.  ``material`` is uint8[nz, ny, nx]."""
+    """A lattice description for the oracle.  ``material`` is uint8[nz, ny, nx];
+    ``collision`` BGK or TRT (with ``magic`` = Lambda)."""
     descriptor: int
     material: np.ndarray
     tau: float
@@ -163,6 +179,8 @@ class Lattice:
     force: tuple = (0.0, 0.0, 0.0)
     gamma: Optional[np.ndarray] = None
     wall_u: np.ndarray = field(default_factory=lambda: np.zeros((256, 3)))
+    collision: int = BGK
+    magic: float = 0.25
 
     def __post_init__(self):
         self.material = np.ascontiguousarray(self.material, np.uint8)
@@ -184,9 +202,9 @@ class Lattice:
     def _c(self) -> _Lattice:
         nz, ny, nx = self.material.shape
         F = (ctypes.c_double * 3)(*[float(v) for v in (list(self.force) + [0, 0, 0])[:3]])
-        self._keep = _Lattice(self.descriptor, nx, ny, nz, self.periodic, 0,
+        self._keep = _Lattice(self.descriptor, nx, ny, nz, self.periodic, int(self.collision),
                               self.material.ctypes.data, self.wall_u.ctypes.data,
-                              float(self.tau), F, _p(self.gamma))
+                              float(self.tau), F, _p(self.gamma), float(self.magic))
         return self._keep
 
     def _f(self, f: np.ndarray) -> np.ndarray:
