@@ -121,8 +121,22 @@ int olb_set_material(olb_handle h, const uint8_t* material, unsigned periodic_ma
  * the fluid cell before collision (BounceBackVelocity). */
 int olb_set_wall_velocity(olb_handle h, int material_id, const double u[3]);
 
-/* BGK relaxation time (omega = 1/tau).  Errors: OLB_ERR_ARG unless tau > 1/2. */
+/* BGK relaxation time (omega = 1/tau); selects the BGK collision.
+ * Errors: OLB_ERR_ARG unless tau > 1/2. */
 int olb_set_bgk(olb_handle h, double tau);
+
+/* Selects the TRT collision (collision::TRT of the guide's dynamics tuples,
+ * section "Dynamics", which names the operator without printing it; read as the
+ * two-relaxation-time operator).  For each pair (i, opp(i)) the even part
+ * (f_i + f_opp(i))/2 relaxes to the even part of f^eq at omega+ = 1/tau (which
+ * sets the viscosity nu = (tau - 1/2)/3), the odd part at omega- given by the
+ * magic parameter Lambda = (1/omega+ - 1/2)(1/omega- - 1/2); the Guo source is
+ * split the same way.  Lambda = (tau - 1/2)^2 is BGK; Lambda = 3/16 puts halfway
+ * bounce-back walls exactly at the wall for Poiseuille flow at every tau.
+ * olb_set_bgk switches back.  olb_adjoint_run and olb_adjoint_run_misfit return
+ * OLB_ERR_UNSUPPORTED while TRT is selected (the adjoint is written for BGK).
+ * Errors: OLB_ERR_ARG unless tau > 1/2 and magic > 0. */
+int olb_set_trt(olb_handle h, double tau, double magic);
 
 /* Uniform body force density F (Guo forcing with u = (j + F/2)/rho, Eqs. FBD, dF). */
 int olb_set_force(olb_handle h, const double F[3]);
@@ -189,7 +203,7 @@ typedef struct {
  * be NULL.  Device memory: (ceil(n/K) + K) copies of the state plus two adjoint
  * fields (K = checkpoint_every).
  * Errors: OLB_ERR_ARG (n_steps < 1, K < 1, bad objective or empty plane),
- *         OLB_ERR_OOM. */
+ *         OLB_ERR_UNSUPPORTED (TRT collision selected), OLB_ERR_OOM. */
 int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
                     const olb_objective* obj, double* loss, double* dL_dgamma,
                     double* dL_dtau);
@@ -208,7 +222,7 @@ int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
  * Outputs as olb_adjoint_run: loss = J, dL_dgamma = dJ/dgamma (double [cells],
  * device or host), dL_dtau = dJ/dtau.
  * Errors: OLB_ERR_ARG (n_steps < 1, K < 1, NULL u_target, region without fluid
- *         cells), OLB_ERR_OOM. */
+ *         cells), OLB_ERR_UNSUPPORTED (TRT collision selected), OLB_ERR_OOM. */
 int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
                            const double* u_target, const uint8_t* region, double* loss,
                            double* dL_dgamma, double* dL_dtau);

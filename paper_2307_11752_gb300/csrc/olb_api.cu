@@ -245,6 +245,8 @@ struct olb_lattice {
   double h_wall[256][4];
   float h_wall_f[256][20];  // 6 w_i (c_i . u_w), computed in FP64 and rounded once
   double tau = 1.0, F[3] = {0.0, 0.0, 0.0};
+  bool trt = false;     // collision operator: BGK, or TRT with magic parameter `magic`
+  double magic = 0.25;
   bool has_gamma = false;
   int64_t time = 0, launches = 0;
 
@@ -266,6 +268,8 @@ struct olb_lattice {
     p.wall_f = reinterpret_cast<const float*>(static_cast<const char*>(wall_u.p) + sizeof(h_wall));
     p.moving = moving ? 1 : 0;
     p.omega = 1.0 / tau;
+    p.trt = trt ? 1 : 0;
+    p.omega_minus = trt ? 1.0 / (magic / (tau - 0.5) + 0.5) : p.omega;
     for (int a = 0; a < 3; ++a) p.force[a] = F[a];
     p.forced = (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0) ? 1 : 0;
     p.gamma = has_gamma ? gamma.p : nullptr;
@@ -768,6 +772,18 @@ int olb_set_bgk(olb_handle h, double tau) {
   if (rc) return rc;
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail(OLB_ERR_ARG, "tau must be > 1/2 (got %g)", tau);
   h->tau = tau;
+  h->trt = false;
+  return OLB_OK;
+}
+
+int olb_set_trt(olb_handle h, double tau, double magic) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(OLB_ERR_ARG, "tau must be > 1/2 (got %g)", tau);
+  if (!(magic > 0.0) || !std::isfinite(magic)) return fail(OLB_ERR_ARG, "magic parameter must be > 0 (got %g)", magic);
+  h->tau = tau;
+  h->magic = magic;
+  h->trt = true;
   return OLB_OK;
 }
 
@@ -958,6 +974,7 @@ int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t K, const olb_objectiv
   int rc = check(h);
   if (rc) return rc;
   if (n_steps < 1 || K < 1) return fail(OLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+  if (h->trt) return fail(OLB_ERR_UNSUPPORTED, "the adjoint is written for the BGK collision");
   if (!obj || obj->plane_axis < 0 || obj->plane_axis >= h->dim || obj->component < 0 || obj->component >= h->dim)
     return fail(OLB_ERR_ARG, "bad objective");
   const int ext[3] = {h->nx, h->ny, h->nz};
@@ -985,6 +1002,7 @@ int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t K, const doubl
   int rc = check(h);
   if (rc) return rc;
   if (n_steps < 1 || K < 1) return fail(OLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+  if (h->trt) return fail(OLB_ERR_UNSUPPORTED, "the adjoint is written for the BGK collision");
   if (!u_target) return fail(OLB_ERR_ARG, "null target velocity");
   const size_t n = (size_t)h->ncell;
   // the region on the host, to count its fluid cells before any work is queued

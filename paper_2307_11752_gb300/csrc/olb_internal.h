@@ -36,6 +36,8 @@ struct HostParams {
   const float* wall_f;    // [256][20] 6 w_i (c_i . u_w) per material and direction, FP32
   int moving;             // a moving-wall material touches the fluid
   double omega;
+  int trt;                // collision: 0 BGK, 1 TRT
+  double omega_minus;     // TRT odd-part rate (from tau and the magic parameter)
   double force[3];
   int forced;
   const void* gamma;      // per-cell porosity in the compute type, or nullptr

@@ -179,6 +179,7 @@ struct Params {
   const double* __restrict__ wall_u;  // [256][4]
   int moving;
   C omega, half_force[3], force[3];
+  C omega_minus;  // TRT: relaxation rate of the odd part (omega is the even rate)
   int forced;
   const C* __restrict__ gamma;
   // per cell: bit i set when x + c_i is a non-fluid cell of the lattice (a wall
@@ -210,6 +211,7 @@ Params<C> to_params(const HostParams& h) {
   p.wall_f = h.wall_f;
   p.moving = h.moving;
   p.omega = (C)h.omega;
+  p.omega_minus = (C)h.omega_minus;
   for (int a = 0; a < 3; ++a) {
     p.force[a] = (C)h.force[a];
     p.half_force[a] = (C)(0.5 * h.force[a]);
@@ -388,7 +390,12 @@ __device__ __forceinline__ void moments(const C (&f)[L::Q], C& drho, C (&j)[3]) 
 
 // BGK collision (+ Guo forcing, + porosity) in place.  Returns rho and the
 // unscaled velocity u = (j + F/2)/rho through the out parameters.
-template <class L, class C>
+// TRT = true: the two-relaxation-time operator (collision::TRT of the dynamics
+// tuples, section "Dynamics"): for each pair (i, opp(i)) the even part
+// f+ = (f_i + f_opp(i))/2 relaxes to the even part of f^eq at omega, the odd part
+// f- at omega_minus, and the Guo source is split the same way with factors
+// (1 - omega/2) and (1 - omega_minus/2).
+template <class L, class C, bool TRT = false>
 __device__ __forceinline__ void collide(const Params<C>& p, C gamma, C (&f)[L::Q], C drho,
                                         const C (&j)[3], C& rho_out, C (&u_out)[3]) {
   const C rho = C(1) + drho;
@@ -431,6 +438,20 @@ __device__ __forceinline__ void collide(const Params<C>& p, C gamma, C (&f)[L::Q
     }
     const C sym = wk * (drho + rho * (C(4.5) * cu * cu) - rs);
     const C anti = wk * C(3) * rho * cu;
+    if (TRT) {
+      const C om_m = p.omega_minus;
+      const C even = om * (C(0.5) * (f[kp] + f[k]) - sym);
+      const C odd = om_m * (C(0.5) * (f[kp] - f[k]) - anti);
+      f[kp] -= even + odd;
+      f[k] -= even - odd;
+      if (p.forced) {
+        const C gs = gf * wk * (C(9) * cu * cF - C(3) * uF);
+        const C ga = (C(1) - C(0.5) * om_m) * wk * C(3) * cF;
+        f[kp] += gs + ga;
+        f[k] += gs - ga;
+      }
+      continue;
+    }
     f[kp] += om * (sym + anti - f[kp]);
     f[k] += om * (sym - anti - f[k]);
     if (p.forced) {
@@ -598,7 +619,7 @@ __device__ __forceinline__ bool on_edge(const Params<C>& p, int x, int y, int z)
 // the cell; it collides and stores.  Links leaving the domain (only when some
 // fluid cell touches a non-periodic domain face) are recognised from the
 // coordinates, again without waiting for a load.
-template <class L, class S, int G, int SC, bool STATS>
+template <class L, class S, int G, int SC, bool STATS, bool TRT>
 __global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typename Store<S>::C> p,
                                                                   const S* src, S* dst,
                                                                   double* partials) {
@@ -618,7 +639,7 @@ __global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typena
     if (edge) gather_outside<L, S, G>(p, src, n, f);
     C drho, j[3], rho, u[3];
     moments<L>(f, drho, j);
-    collide<L>(p, gamma, f, drho, j, rho, u);
+    collide<L, C, TRT>(p, gamma, f, drho, j, rho, u);
     if (w & kWordFluid) {
       const uint32_t pm = w & (kWordLinks | kWordMoving);
       const int cls = edge ? 3 : (pm ? 2 : 1);
@@ -1026,7 +1047,7 @@ struct Launch {
     return p;
   }
 
-  template <int G, int SC, bool STATS>
+  template <int G, int SC, bool STATS, bool TRT>
   static cudaError_t step_t(const HostParams& h, const void* src, void* dst, double* partials) {
     if constexpr (!std::is_same<S, double>::value) {
       if (pairs_ok(h.nx)) {
@@ -1045,26 +1066,29 @@ struct Launch {
         if (h.cls == nullptr && !OLB_FORCE_WALLS) {  // all fluid, all periodic
           Planes<S, false> pl;
           fill(pl);
-          k_step_pair<L, S, G, SC, STATS, false><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
+          k_step_pair<L, S, G, SC, STATS, false, TRT><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
         } else {
           Planes<S, true> pl;
           pl.lead = 0;
           fill(pl);
-          k_step_pair<L, S, G, SC, STATS, true><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
+          k_step_pair<L, S, G, SC, STATS, true, TRT><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
         }
         return cudaGetLastError();
       }
     }
     const StepGrid g = make_step_grid(h, false);
-    k_step<L, S, G, SC, STATS><<<g.dims(), 256, 0, h.stream>>>(
+    k_step<L, S, G, SC, STATS, TRT><<<g.dims(), 256, 0, h.stream>>>(
         params(h), static_cast<const S*>(src), static_cast<S*>(dst), partials);
     return cudaGetLastError();
   }
   template <int G, int SC>
   static cudaError_t step_s(const HostParams& h, bool stats, const void* src, void* dst,
                             double* partials) {
-    return stats ? step_t<G, SC, true>(h, src, dst, partials)
-                 : step_t<G, SC, false>(h, src, dst, partials);
+    if (h.trt)
+      return stats ? step_t<G, SC, true, true>(h, src, dst, partials)
+                   : step_t<G, SC, false, true>(h, src, dst, partials);
+    return stats ? step_t<G, SC, true, false>(h, src, dst, partials)
+                 : step_t<G, SC, false, false>(h, src, dst, partials);
   }
   static cudaError_t step(const HostParams& h, int gather, int scatter, bool stats,
                           const void* src, void* dst, double* partials) {

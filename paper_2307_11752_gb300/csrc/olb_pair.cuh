@@ -164,7 +164,8 @@ __device__ __forceinline__ void st_pair(S* plane, const PairNbr& n, int dx, int 
 //   f*_s = f_s + omega (feq_s - f_s) + (1 - omega/2) Guo_s.
 // Returns rho_s and u for the wall terms and statistics.
 // ---------------------------------------------------------------------------------
-template <class L, int SCALE_NUM>
+// TRT = true: the two-relaxation-time operator (see collide in olb_kernels.cuh).
+template <class L, int SCALE_NUM, bool TRT = false>
 __device__ __forceinline__ void collide_pair(const Params<float>& p, F2 gamma, F2 (&f)[L::Q], F2& drho_s,
                                              F2 (&j_s)[3], F2& rho_s, F2 (&u)[3]) {
   constexpr float SCALE = (float)SCALE_NUM;
@@ -241,12 +242,21 @@ __device__ __forceinline__ void collide_pair(const Params<float>& p, F2 gamma, F
     }
     const F2 sym = F2(wk) * fma2(B, cu * cu, A);
     const F2 anti = F2(wk) * T * cu;
-    F2 fp = fma2(one_m_om, f[kp], omv * (sym + anti));
-    F2 fm = fma2(one_m_om, f[k], omv * (sym - anti));
+    F2 fp, fm;
+    if (TRT) {
+      // even = omega (f+ - sym), odd = omega_minus (f- - anti), f+- = (f_kp +- f_k)/2
+      const F2 even = omv * fma2(F2(0.5f), f[kp] + f[k], neg(sym));
+      const F2 odd = F2(p.omega_minus) * fma2(F2(0.5f), f[kp] - f[k], neg(anti));
+      fp = f[kp] - (even + odd);
+      fm = f[k] - (even - odd);
+    } else {
+      fp = fma2(one_m_om, f[kp], omv * (sym + anti));
+      fm = fma2(one_m_om, f[k], omv * (sym - anti));
+    }
     if (p.forced) {
       // Guo: gf w (9 cu cF - 3 u'.F) +- 3 gf w cF   (F in scaled units)
       const F2 gs = fma2(F2(9.0f * gf * wk * cFs), cu, F2(-3.0f * gf * wk) * uF);
-      const float ga = 3.0f * gf * wk * cFs;
+      const float ga = 3.0f * (TRT ? 1.0f - 0.5f * p.omega_minus : gf) * wk * cFs;
       fp = fp + gs + F2(ga);
       fm = fm + gs - F2(ga);
     }
@@ -337,7 +347,7 @@ __device__ __forceinline__ void ghost_stores(const Params<float>& p, const P& pl
 // are all fluid with every axis periodic: it carries no boundary code at all, so
 // the boundary paths cannot cost registers or scheduling freedom there.
 // ---------------------------------------------------------------------------------
-template <class L, class S, int G, int SC, bool STATS, bool WALLS>
+template <class L, class S, int G, int SC, bool STATS, bool WALLS, bool TRT>
 __global__ void __launch_bounds__(256, WALLS ? PairStore<S>::MIN_BLOCKS_WALLS : PairStore<S>::MIN_BLOCKS) k_step_pair(Params<float> p,
                                                                              const __grid_constant__ Planes<S, WALLS> pl,
                                                                              double* partials) {
@@ -396,7 +406,7 @@ __global__ void __launch_bounds__(256, WALLS ? PairStore<S>::MIN_BLOCKS_WALLS : 
       }
     }
     F2 drho, j[3], rho, u[3];
-    collide_pair<L, SC_NUM>(p, gamma, f, drho, j, rho, u);
+    collide_pair<L, SC_NUM, TRT>(p, gamma, f, drho, j, rho, u);
     const bool fl0 = (w[0] & kWordFluid) != 0, fl1 = (w[1] & kWordFluid) != 0;
     if (!WALLS) {
       // every cell fluid, every axis periodic: plain paired stores only

@@ -42,6 +42,7 @@ SIGNATURES = {
     "olb_set_material": [_P, _P, _U],
     "olb_set_wall_velocity": [_P, _I, _P],
     "olb_set_bgk": [_P, _D],
+    "olb_set_trt": [_P, _D, _D],
     "olb_set_force": [_P, _P],
     "olb_set_porosity": [_P, _P],
     "olb_init_equilibrium": [_P, _P, _P],
@@ -232,6 +233,10 @@ class Lattice:
 
     def set_bgk(self, tau: float):
         _call("olb_set_bgk", self.handle, float(tau))
+
+    def set_trt(self, tau: float, magic: float = 0.25):
+        """TRT collision: viscosity from tau, odd-part rate from the magic parameter."""
+        _call("olb_set_trt", self.handle, float(tau), float(magic))
 
     def set_force(self, F):
         FF = (ctypes.c_double * 3)(*[float(v) for v in (list(F) + [0, 0, 0])[:3]])

@@ -22,6 +22,8 @@ class Case:
     rho: Optional[np.ndarray] = None
     u: Optional[np.ndarray] = None
     noise: Optional[np.ndarray] = None
+    collision: str = "bgk"   # or "trt" with magic parameter `magic`
+    magic: float = 0.25
 
     @property
     def shape(self):
@@ -39,7 +41,9 @@ class Case:
 
     def oracle(self, oracle):
         return oracle.Lattice(self.d, self.material, self.tau, periodic=self.periodic,
-                              force=self.force, gamma=self.gamma, wall_u=self.wall_table())
+                              force=self.force, gamma=self.gamma, wall_u=self.wall_table(),
+                              collision=oracle.TRT if self.collision == "trt" else oracle.BGK,
+                              magic=self.magic)
 
     def oracle_state(self, lat):
         rho, u = (self.rho, self.u) if self.rho is not None else I.rest(self.shape)
@@ -57,7 +61,10 @@ class Case:
         lat.set_material(torch.from_numpy(self.material.reshape(-1).copy()).cuda(), self.periodic)
         for k, v in self.walls.items():
             lat.set_wall_velocity(k, v)
-        lat.set_bgk(self.tau)
+        if self.collision == "trt":
+            lat.set_trt(self.tau, self.magic)
+        else:
+            lat.set_bgk(self.tau)
         lat.set_force(self.force)
         if self.gamma is not None:
             lat.set_porosity(torch.from_numpy(self.gamma.reshape(-1).copy()).cuda())
