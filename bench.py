@@ -250,6 +250,17 @@ def variants(olb, torch):
             "MLUPS": round(fluid / ms / 1e3, 1), "bytes_per_update": b,
             "roofline_frac": round(fluid * b / (ms * 1e-3) / 1e9 / peak, 4)}
         lat.close()
+    # the same cavity with the TRT collision (magic parameter 3/16)
+    for dtype in ("f32", "f16"):
+        lat, m, noise = make_cavity(olb, torch, dtype, "pull")
+        lat.set_trt(I.cavity_tau(N_SIDE, 400.0, LID), 3.0 / 16.0)
+        run_workload(lat, noise, 200)
+        ms = time_step_kernel(torch, lat, 400)
+        b = 19 * 2 * olb.STATE_ELEM[olb.DTYPES[dtype]]
+        out[f"cavity128_{dtype}_pull_trt"] = {
+            "MLUPS": round(fluid / ms / 1e3, 1), "bytes_per_update": b,
+            "roofline_frac": round(fluid * b / (ms * 1e-3) / 1e9 / peak, 4)}
+        lat.close()
     # 3D Taylor-Green vortex 512^3, periodic (no wall cells)
     n = 512
     for dtype in ("f32", "f16"):
@@ -357,6 +368,59 @@ def experiment_adjoint384(torch, olb, fd_cells=4):
     res["fd_dtau"] = {"fd": d, "f16_rel": abs(grads["f16"][2] - d) / abs(d), "f32_rel": abs(grads["f32"][2] - d) / abs(d)}
     ref.close()
     return res
+
+
+def experiment_fd256(torch, olb, cells=64):
+    """The differentiable channel at its full size: 256x128x128, FP32 storage, 2000
+    steps, checkpoints every 100, loss = mean u_x on the outlet plane x = 255.  The
+    adjoint's dL/dgamma at `cells` seeded random fluid cells and dL/dtau against
+    central differences of FP64 forward runs on the GPU (h = 1e-5 for gamma, 1e-6 for
+    tau)."""
+    nx, ny, nz, steps, K = 256, 128, 128, 2000, 100
+    obj = (0, nx - 1, 0)
+    lat, m = porous_channel(olb, torch, nx, ny, nz, "f32")
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    loss, dg, dtau = lat.adjoint_run(steps, K, obj)
+    torch.cuda.synchronize()
+    adj_sec = time.perf_counter() - t
+    dg = dg.cpu().numpy().reshape(-1)
+    lat.close()
+    torch.cuda.empty_cache()
+    gamma = I.smoothed_porosity(2, m)
+    ref = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype="f64", scheme="pull")
+    ref.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 1)
+    ref.set_force((I.channel_force(ny, 0.8), 0, 0))
+    plane = torch.from_numpy(m[:, :, nx - 1] == I.FLUID).cuda()
+
+    def run(gam, tau):
+        ref.set_bgk(tau)
+        ref.set_porosity(torch.from_numpy(gam.reshape(-1)).cuda())
+        ref.init_equilibrium()
+        ref.step(steps)
+        _, u = ref.moments()
+        return float(u[0, :, :, nx - 1][plane].mean())
+
+    t = time.perf_counter()
+    rel = []
+    for c in I.random_fluid_cells(3, m, cells):
+        gp = gamma.reshape(-1).copy()
+        gm = gp.copy()
+        gp[c] += 1e-5
+        gm[c] -= 1e-5
+        d = (run(gp, 0.8) - run(gm, 0.8)) / 2e-5
+        rel.append(abs(dg[c] - d) / abs(d))
+    d = (run(gamma, 0.8 + 1e-6) - run(gamma, 0.8 - 1e-6)) / 2e-6
+    ref.close()
+    rel = np.array(rel)
+    return {
+        "workload": f"porous channel {nx}x{ny}x{nz}, FP32 storage, {steps} steps, K={K}, loss = mean u_x on x = {nx - 1}",
+        "adjoint_seconds": round(adj_sec, 2), "loss": loss, "dL_dtau": dtau,
+        "fd_cells": int(len(rel)), "fd_seconds": round(time.perf_counter() - t, 1),
+        "dgamma_rel_err_max": float(rel.max()), "dgamma_rel_err_median": float(np.median(rel)),
+        "dgamma_cells_within_1e-4": int((rel <= 1e-4).sum()),
+        "dtau_fd": d, "dtau_rel_err": abs(dtau - d) / abs(d),
+    }
 
 
 def experiment_domain_id(torch, olb, dtype="f32", iterations=20):
@@ -575,7 +639,7 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--experiment", choices=["adjoint384", "domain_id"], default=None,
+    ap.add_argument("--experiment", choices=["adjoint384", "domain_id", "fd256"], default=None,
                     help="run a named experiment instead of the benchmark and print its JSON")
     args = ap.parse_args()
     if args.experiment is not None:
@@ -584,7 +648,8 @@ def main():
         from paper_2307_11752_gb300 import build, olb
         build.build()
         olb.load()
-        run = {"adjoint384": experiment_adjoint384, "domain_id": experiment_domain_id}[args.experiment]
+        run = {"adjoint384": experiment_adjoint384, "domain_id": experiment_domain_id,
+               "fd256": experiment_fd256}[args.experiment]
         print(json.dumps(run(torch, olb)), flush=True)
         return
     if args.impl == "reference":
