@@ -27,6 +27,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -72,7 +73,10 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples next to the run's other outputs when OLB_CLOCKS_DIR is set, else in
+        # the temp directory; the JSON line carries their summary
+        self.path = os.path.join(os.environ.get("OLB_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"olb_clocks_rank{index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

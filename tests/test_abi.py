@@ -23,7 +23,7 @@ def libpath():
     return build.build()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_calls():
     names = _declared()
     for required in ("olb_lattice_create", "olb_set_material", "olb_set_bgk", "olb_step",
                      "olb_moments", "olb_adjoint_run"):
