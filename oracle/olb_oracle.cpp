@@ -408,8 +408,13 @@ T loss_of(const olb_oracle_lattice* L, const T* f, const std::vector<int64_t>& c
 // Jacobian of one collision, J[k][i] = d f*_k / d f_i, plus d f*/d gamma and
 // d f*/d omega, written out from the collision formula by the chain rule through
 // rho, u = (j + F/2)/rho and u' = gamma u.
+//   BGK (trt = false): f*_k = f_k + omega (feq_k - f_k) + (1 - omega/2) S_k.
+//   TRT (trt = true):  the even parts relax at omega, the odd parts at omega_m, and
+//   omega_m depends on omega through the magic parameter (d omega_m / d omega =
+//   domega_m), so d f*/d omega includes that chain.
 void collision_jacobian(const Desc& D, const double* f, double gamma, double omega,
-                        const double F[3], double J[19][19], double dg[19], double dw[19]) {
+                        const double F[3], double J[19][19], double dg[19], double dw[19],
+                        bool trt = false, double omega_m = 0.0, double domega_m = 0.0) {
   double rho, j[3], u[3];
   moments(D, f, F, rho, j, u);
   double up[3] = {gamma * u[0], gamma * u[1], gamma * u[2]};
@@ -417,6 +422,8 @@ void collision_jacobian(const Desc& D, const double* f, double gamma, double ome
   equilibrium(D, rho, up, feq);
   double uF = up[0] * F[0] + up[1] * F[1] + up[2] * F[2];
   double cs2 = D.cs2;
+  // d feq_k / d f_i, d S_k / d f_i, and their gamma derivatives; S_k itself
+  double Ep[19][19], Sp[19][19], Eg[19], Sg[19], S[19];
   for (int k = 0; k < D.q; ++k) {
     double cu = D.c[k][0] * up[0] + D.c[k][1] * up[1] + D.c[k][2] * up[2];
     double cF = D.c[k][0] * F[0] + D.c[k][1] * F[1] + D.c[k][2] * F[2];
@@ -428,18 +435,45 @@ void collision_jacobian(const Desc& D, const double* f, double gamma, double ome
       dS_du[a] = D.w[k] * (-F[a] / cs2 + D.c[k][a] * cF / (cs2 * cs2));
     }
     for (int i = 0; i < D.q; ++i) {
-      double v = (k == i ? 1.0 - omega : 0.0) + omega * dE_drho;
+      double e = dE_drho, sd = 0.0;
       for (int a = 0; a < 3; ++a) {
         double du_df = gamma * (D.c[i][a] - u[a]) / rho;  // d u'_a / d f_i
-        v += (omega * dE_du[a] + (1.0 - 0.5 * omega) * dS_du[a]) * du_df;
+        e += dE_du[a] * du_df;
+        sd += dS_du[a] * du_df;
       }
-      J[k][i] = v;
+      Ep[k][i] = e;
+      Sp[k][i] = sd;
     }
-    double g = 0.0;
-    for (int a = 0; a < 3; ++a) g += (omega * dE_du[a] + (1.0 - 0.5 * omega) * dS_du[a]) * u[a];
-    dg[k] = g;
-    double S = D.w[k] * ((cF - uF) / cs2 + cu * cF / (cs2 * cs2));
-    dw[k] = -f[k] + feq[k] - 0.5 * S;
+    Eg[k] = dE_du[0] * u[0] + dE_du[1] * u[1] + dE_du[2] * u[2];
+    Sg[k] = dS_du[0] * u[0] + dS_du[1] * u[1] + dS_du[2] * u[2];
+    S[k] = D.w[k] * ((cF - uF) / cs2 + cu * cF / (cs2 * cs2));
+  }
+  if (!trt) {
+    for (int k = 0; k < D.q; ++k) {
+      for (int i = 0; i < D.q; ++i)
+        J[k][i] = (k == i ? 1.0 - omega : 0.0) + omega * Ep[k][i] + (1.0 - 0.5 * omega) * Sp[k][i];
+      dg[k] = omega * Eg[k] + (1.0 - 0.5 * omega) * Sg[k];
+      dw[k] = -f[k] + feq[k] - 0.5 * S[k];
+    }
+    return;
+  }
+  const double gp = 1.0 - 0.5 * omega, gm = 1.0 - 0.5 * omega_m;
+  for (int k = 0; k < D.q; ++k) {
+    const int o = D.opp[k];
+    for (int i = 0; i < D.q; ++i) {
+      // even and odd parts of the identity, of feq' and of S'
+      double Ie = 0.5 * ((k == i ? 1.0 : 0.0) + (o == i ? 1.0 : 0.0));
+      double Io = 0.5 * ((k == i ? 1.0 : 0.0) - (o == i ? 1.0 : 0.0));
+      double Ee = 0.5 * (Ep[k][i] + Ep[o][i]), Eo = 0.5 * (Ep[k][i] - Ep[o][i]);
+      double Se = 0.5 * (Sp[k][i] + Sp[o][i]), So = 0.5 * (Sp[k][i] - Sp[o][i]);
+      J[k][i] = (k == i ? 1.0 : 0.0) - omega * (Ie - Ee) - omega_m * (Io - Eo) + gp * Se + gm * So;
+    }
+    dg[k] = omega * 0.5 * (Eg[k] + Eg[o]) + omega_m * 0.5 * (Eg[k] - Eg[o]) + gp * 0.5 * (Sg[k] + Sg[o]) +
+            gm * 0.5 * (Sg[k] - Sg[o]);
+    // d f*_k / d omega (even part) and d f*_k / d omega_m (odd part)
+    double d_even = -(0.5 * (f[k] + f[o]) - 0.5 * (feq[k] + feq[o])) - 0.25 * (S[k] + S[o]);
+    double d_odd = -(0.5 * (f[k] - f[o]) - 0.5 * (feq[k] - feq[o])) - 0.25 * (S[k] - S[o]);
+    dw[k] = d_even + d_odd * domega_m;
   }
 }
 
@@ -488,6 +522,12 @@ void collide_transpose(const olb_oracle_lattice* L, const double* f, const doubl
   Geo g(L);
   const Desc& D = *g.D;
   double omega = 1.0 / L->tau;
+  // TRT: omega_m(omega) at fixed magic Lambda; with a = 1/omega - 1/2,
+  // omega_m = 1/(Lambda/a + 1/2) and d omega_m / d omega = -omega_m^2 Lambda / (a^2 omega^2)
+  const bool trt = L->collision == 1;
+  const double omega_m = trt ? omega_minus(omega, L->magic) : omega;
+  const double a = 1.0 / omega - 0.5;
+  const double domega_m = trt ? -omega_m * omega_m * L->magic / (a * a * omega * omega) : 1.0;
   std::vector<double> dw_cell(g.n, 0.0);
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < g.n; ++c) {
@@ -498,7 +538,7 @@ void collide_transpose(const olb_oracle_lattice* L, const double* f, const doubl
     double fc[19], J[19][19], dg[19], dwk[19];
     for (int i = 0; i < D.q; ++i) fc[i] = f[i * g.n + c];
     double gam = L->gamma ? L->gamma[c] : 1.0;
-    collision_jacobian(D, fc, gam, omega, L->force, J, dg, dwk);
+    collision_jacobian(D, fc, gam, omega, L->force, J, dg, dwk, trt, omega_m, domega_m);
     double gsum = 0.0, wsum = 0.0;
     for (int i = 0; i < D.q; ++i) {
       double v = 0.0;
@@ -707,7 +747,7 @@ int olb_oracle_collide_tangent(const olb_oracle_lattice* L, const double* f, con
 //   lam = (dC/df)^T lams;  dgamma += (dC/dgamma)^T lams;  dtau += (dC/dtau)^T lams
 int olb_oracle_collide_adjoint(const olb_oracle_lattice* L, const double* f,
                                const double* lams, double* lam, double* dgamma, double* dtau) {
-  if (!valid(L) || L->collision != 0) return -1;  // the Jacobian is written out for BGK
+  if (!valid(L)) return -1;
   double domega = 0.0;
   collide_transpose(L, f, lams, lam, dgamma, &domega);
   if (dtau) *dtau += -domega / (L->tau * L->tau);
@@ -733,7 +773,7 @@ int olb_oracle_stream_adjoint(const olb_oracle_lattice* L, const double* lam, do
 int olb_oracle_adjoint(const olb_oracle_lattice* L, const double* f0, int64_t nsteps,
                        const olb_oracle_objective* obj, double* loss, double* dgamma,
                        double* dtau, double* lambda0) {
-  if (!valid(L) || nsteps < 0 || L->collision != 0) return -1;  // BGK Jacobian only
+  if (!valid(L) || nsteps < 0) return -1;
   Geo g(L);
   const Desc& D = *g.D;
   std::vector<int64_t> cells;

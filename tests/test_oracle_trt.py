@@ -10,6 +10,8 @@ part and omega- set by the magic parameter Lambda = (1/omega+ - 1/2)(1/omega- - 
 * Force-driven Poiseuille flow between halfway bounce-back walls is the exact
   parabola with its zeros on the walls for Lambda = 3/16 at every tau (the known
   property of the TRT operator); BGK has that only at tau = 1/2 + sqrt(3/16).
+* Its discrete adjoint (explicit Jacobian) against dual numbers and central
+  differences.
 """
 import math
 
@@ -118,11 +120,95 @@ def test_trt_poiseuille_exact_at_magic_3_16(oracle, d, tau):
         assert np.max(np.abs(pb - exact)) > 1e-4 * exact.max()
 
 
-def test_trt_rejected_by_the_bgk_adjoint(oracle):
-    m = I.channel(8, 6, 1)
-    lat = oracle.Lattice(0, m, 0.8, periodic=1, collision=oracle.TRT, magic=0.25)
-    f0 = lat.init_equilibrium(*I.rest(m.shape))
-    with pytest.raises(ValueError):
-        lat.adjoint(f0, 3, (0, 7, 0))
+def test_trt_rejects_a_non_positive_magic_parameter(oracle):
     with pytest.raises(ValueError):
         oracle.collide_cell_trt(0, np.ones(9) / 9, 0.8, 0.0)
+    m = I.channel(8, 6, 1)
+    lat = oracle.Lattice(0, m, 0.8, periodic=1, collision=oracle.TRT, magic=-1.0)
+    with pytest.raises(ValueError):
+        lat.step(lat.init_equilibrium(*I.rest(m.shape)), 1)
+
+
+# ---------------------------------------------------------------------------------
+# The discrete adjoint of the TRT map (the explicit Jacobian of the oracle), pinned
+# like the BGK one: transpose identity against dual numbers, tangent-linear of the
+# whole run, central differences.  d/dtau holds Lambda fixed (omega- follows omega+).
+# ---------------------------------------------------------------------------------
+def _trt_channel(oracle, d, shape, moving=False, magic=3.0 / 16.0, tau=0.7):
+    from test_oracle_adjoint import _porous_channel
+
+    lat, f0 = _porous_channel(oracle, d, shape, tau=tau, moving=moving)
+    lat.collision = oracle.TRT
+    lat.magic = magic
+    return lat, f0
+
+
+@pytest.mark.parametrize("d,magic", [(0, 3.0 / 16.0), (1, 3.0 / 16.0), (1, 1.0)])
+def test_trt_collision_transpose_identity(oracle, d, magic):
+    shape = (1, 6, 7) if d == 0 else (4, 5, 6)
+    lat, f = _trt_channel(oracle, d, shape, magic=magic)
+    q = lat.q
+    v = I.uniform(171, (q,) + shape) - 0.5
+    vg = I.uniform(172, shape) - 0.5
+    vt = 0.3
+    w = I.uniform(173, (q,) + shape) - 0.5
+    fl = lat.material == I.FLUID
+    w[:, ~fl] = 0.0
+    Jv = lat.collide_tangent(f, v, dgamma=vg, dtau=vt)
+    lam, dg, dt = lat.collide_adjoint(f, w)
+    lhs = float((Jv * w).sum())
+    rhs = float((v * lam).sum() + (vg * dg).sum() + vt * dt)
+    assert abs(lhs - rhs) <= 1e-14 * abs(lhs)
+    # the tau part alone (the chain through omega-)
+    lhs_t = float((lat.collide_tangent(f, np.zeros_like(v), dtau=1.0) * w).sum())
+    assert abs(lhs_t - dt) <= 1e-13 * abs(lhs_t)
+
+
+@pytest.mark.parametrize("d,moving", [(0, False), (1, False), (0, True), (1, True)])
+def test_trt_adjoint_matches_tangent_linear(oracle, d, moving):
+    shape = (1, 8, 10) if d == 0 else (5, 6, 8)
+    lat, f0 = _trt_channel(oracle, d, shape, moving=moving)
+    n = 30
+    fl = lat.material == I.FLUID
+    f = f0.copy()
+    lat.step(f, n)
+    _, u = lat.moments(f)
+    for obj in ((0, shape[2] - 1, 0), oracle.Misfit(u * 1.01 + 1e-4)):
+        loss, dg, dtau = lat.adjoint(f0, n, obj)
+        for k, seed in enumerate((191, 192)):
+            v = np.where(fl, I.uniform(seed, shape) - 0.5, 0.0)
+            s = 0.7 if k == 1 else 0.0
+            loss_t, dl = lat.tangent(f0, n, obj, dgamma=v, dtau=s)
+            assert loss_t == loss
+            pred = float((dg * v).sum() + dtau * s)
+            assert abs(pred - dl) <= 1e-11 * abs(dl), (pred, dl)
+
+
+def test_trt_adjoint_matches_central_differences(oracle):
+    shape = (4, 6, 8)
+    lat, f0 = _trt_channel(oracle, 1, shape, magic=0.3)
+    n = 25
+    obj = (0, shape[2] - 1, 0)
+    loss, dg, dtau = lat.adjoint(f0, n, obj)
+    base = lat.gamma.copy()
+    for c in I.random_fluid_cells(5, lat.material, 5):
+        vals = []
+        for sgn in (1, -1):
+            g = base.copy()
+            g.reshape(-1)[c] += sgn * 1e-5
+            lat.gamma = g
+            f = f0.copy()
+            lat.step(f, n)
+            vals.append(lat.loss(f, obj))
+        lat.gamma = base
+        fd = (vals[0] - vals[1]) / 2e-5
+        assert abs(fd - dg.reshape(-1)[c]) <= 1e-6 * abs(fd) + 1e-14
+    vals = []
+    for sgn in (1, -1):
+        lat.tau = 0.7 + sgn * 1e-6
+        f = f0.copy()
+        lat.step(f, n)
+        vals.append(lat.loss(f, obj))
+    lat.tau = 0.7
+    fd = (vals[0] - vals[1]) / 2e-6
+    assert abs(fd - dtau) <= 1e-6 * abs(fd)
