@@ -824,3 +824,146 @@ int olb_oracle_adjoint(const olb_oracle_lattice* L, const double* f0, int64_t ns
 }
 
 }  // extern "C"
+
+// =================================================================================
+// Advection-diffusion (section "Advection--Diffusion Equation"): BGK on D2Q5 /
+// D3Q7 for a passive scalar C transported by a prescribed velocity v,
+//   g*_i = g_i - omega (g_i - g^eq_i),   g^eq_i = w_i C (1 + c_i . v / cs2),
+//   C = sum_i g_i,  diffusivity mu = cs2 (tau - 1/2),
+// followed by periodic streaming g_i(x + c_i, t + 1) = g*_i(x, t).  The guide
+// prints the first-order equilibrium and names the D2Q5 / D3Q7 descriptors; their
+// tables are read as: rest velocity first, then the face velocities in the D2Q9
+// order (first non-zero component -1 first, opposite at i + (q-1)/2), weights
+// fixed by sum w = 1 and sum w c_a c_b = cs2 delta_ab with the usual
+// cs2 = 1/3 (D2Q5: w = 1/3, 1/6) and cs2 = 1/4 (D3Q7: w = 1/4, 1/8).
+// =================================================================================
+namespace {
+
+struct AdeDesc {
+  int d, q;
+  int c[7][3];
+  int opp[7];
+  double w[7];
+  double cs2;
+};
+
+const AdeDesc kD2Q5 = {
+    2, 5,
+    {{0, 0, 0}, {-1, 0, 0}, {0, -1, 0}, {1, 0, 0}, {0, 1, 0}},
+    {0, 3, 4, 1, 2},
+    {1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0},
+    1.0 / 3.0};
+
+const AdeDesc kD3Q7 = {
+    3, 7,
+    {{0, 0, 0}, {-1, 0, 0}, {0, -1, 0}, {0, 0, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}},
+    {0, 4, 5, 6, 1, 2, 3},
+    {1.0 / 4.0, 1.0 / 8.0, 1.0 / 8.0, 1.0 / 8.0, 1.0 / 8.0, 1.0 / 8.0, 1.0 / 8.0},
+    1.0 / 4.0};
+
+const AdeDesc* ade_descriptor(int d) {
+  if (d == 0) return &kD2Q5;
+  if (d == 1) return &kD3Q7;
+  return nullptr;
+}
+
+// v at cell c: per-cell field [3][n] or the uniform vector
+inline void ade_velocity(const double* v, const double* vu, int64_t n, int64_t c, double out[3]) {
+  for (int a = 0; a < 3; ++a) out[a] = v ? v[a * n + c] : (vu ? vu[a] : 0.0);
+}
+
+void ade_equilibrium(const AdeDesc& D, double C, const double v[3], double* geq) {
+  for (int i = 0; i < D.q; ++i) {
+    double cv = D.c[i][0] * v[0] + D.c[i][1] * v[1] + D.c[i][2] * v[2];
+    geq[i] = D.w[i] * C * (1.0 + cv / D.cs2);
+  }
+}
+
+bool ade_valid(const AdeDesc* D, int nx, int ny, int nz) {
+  if (!D || nx < 1 || ny < 1 || nz < 1) return false;
+  if (D->d == 2 && nz != 1) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Table of D2Q5 (d = 0) or D3Q7 (d = 1): dim, q, c[q][3], opposite[q], w[q], cs2.
+int olb_oracle_ade_descriptor(int d, int* dim, int* q, int* c, int* opp, double* w, double* cs2) {
+  const AdeDesc* D = ade_descriptor(d);
+  if (!D) return -1;
+  *dim = D->d;
+  *q = D->q;
+  for (int i = 0; i < D->q; ++i) {
+    for (int a = 0; a < 3; ++a) c[3 * i + a] = D->c[i][a];
+    opp[i] = D->opp[i];
+    w[i] = D->w[i];
+  }
+  *cs2 = D->cs2;
+  return 0;
+}
+
+// g = g^eq(C, v) on every cell; C [n], v [3][n] or NULL with vu[3] uniform.
+int olb_oracle_ade_init(int d, int nx, int ny, int nz, const double* C, const double* v,
+                        const double* vu, double* g) {
+  const AdeDesc* D = ade_descriptor(d);
+  if (!ade_valid(D, nx, ny, nz) || !C || !g) return -1;
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int64_t c = 0; c < n; ++c) {
+    double vc[3], geq[7];
+    ade_velocity(v, vu, n, c, vc);
+    ade_equilibrium(*D, C[c], vc, geq);
+    for (int i = 0; i < D->q; ++i) g[i * n + c] = geq[i];
+  }
+  return 0;
+}
+
+// nsteps BGK collide-and-stream steps on a fully periodic lattice, in place.
+int olb_oracle_ade_step(int d, int nx, int ny, int nz, double tau, const double* v,
+                        const double* vu, double* g, int64_t nsteps) {
+  const AdeDesc* D = ade_descriptor(d);
+  if (!ade_valid(D, nx, ny, nz) || !(tau > 0.5) || !g || nsteps < 0) return -1;
+  const int64_t n = (int64_t)nx * ny * nz;
+  const double omega = 1.0 / tau;
+  std::vector<double> gs((size_t)D->q * n);
+  for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+      double C = 0.0;
+      for (int i = 0; i < D->q; ++i) C += g[i * n + c];
+      double vc[3], geq[7];
+      ade_velocity(v, vu, n, c, vc);
+      ade_equilibrium(*D, C, vc, geq);
+      for (int i = 0; i < D->q; ++i) gs[i * n + c] = g[i * n + c] - omega * (g[i * n + c] - geq[i]);
+    }
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          const int64_t c = ((int64_t)z * ny + y) * nx + x;
+          for (int i = 0; i < D->q; ++i) {
+            const int tx = (x + D->c[i][0] + nx) % nx;
+            const int ty = (y + D->c[i][1] + ny) % ny;
+            const int tz = (z + D->c[i][2] + nz) % nz;
+            g[i * n + ((int64_t)tz * ny + ty) * nx + tx] = gs[i * n + c];
+          }
+        }
+  }
+  return 0;
+}
+
+// C = sum_i g_i per cell.
+int olb_oracle_ade_density(int d, int nx, int ny, int nz, const double* g, double* C) {
+  const AdeDesc* D = ade_descriptor(d);
+  if (!ade_valid(D, nx, ny, nz) || !g || !C) return -1;
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int64_t c = 0; c < n; ++c) {
+    double s = 0.0;
+    for (int i = 0; i < D->q; ++i) s += g[i * n + c];
+    C[c] = s;
+  }
+  return 0;
+}
+
+}  // extern "C"

@@ -106,6 +106,10 @@ def lib():
             "olb_oracle_collide_adjoint": [P, P, P, P, P, P],
             "olb_oracle_stream_adjoint": [P, P, P, P],
             "olb_oracle_adjoint": [P, P, I64, P, P, P, P, P],
+            "olb_oracle_ade_descriptor": [ctypes.c_int, P, P, P, P, P, P],
+            "olb_oracle_ade_init": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P],
+            "olb_oracle_ade_step": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, P, P, P, I64],
+            "olb_oracle_ade_density": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P],
         }
         for name, args in sig.items():
             fn = getattr(_lib, name)
@@ -304,6 +308,64 @@ class Lattice:
         if want_lambda0:
             return loss.value, dg, dtau.value, lam0
         return loss.value, dg, dtau.value
+
+
+# ------------------------------------------------------------------------------------
+# Advection-diffusion (D2Q5 = 0, D3Q7 = 1), fully periodic
+# ------------------------------------------------------------------------------------
+def ade_descriptor(d: int):
+    """(dim, q, c[q,3], opposite[q], w[q], cs2) of D2Q5 (d = 0) or D3Q7 (d = 1)."""
+    c = np.zeros((7, 3), np.int32)
+    opp = np.zeros(7, np.int32)
+    w = np.zeros(7, np.float64)
+    dim, q, cs2 = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().olb_oracle_ade_descriptor(d, ctypes.byref(dim), ctypes.byref(q), _p(c), _p(opp), _p(w),
+                                           ctypes.byref(cs2)), "ade_descriptor")
+    q = q.value
+    return dim.value, q, c[:q].copy(), opp[:q].copy(), w[:q].copy(), cs2.value
+
+
+@dataclass
+class AdeLattice:
+    """Passive scalar on a periodic D2Q5 / D3Q7 lattice of shape (nz, ny, nx), BGK with
+    relaxation time ``tau`` towards the first-order equilibrium, advected by ``v``
+    (a uniform 3-vector or a [3, nz, ny, nx] field)."""
+    descriptor: int
+    shape: tuple
+    tau: float
+    v: object = (0.0, 0.0, 0.0)
+
+    def __post_init__(self):
+        self.q = ade_descriptor(self.descriptor)[1]
+        v = np.asarray(self.v, np.float64)
+        if v.size == 3:
+            self._vu, self._vf = np.ascontiguousarray(v.reshape(3)), None
+        else:
+            self._vu, self._vf = None, np.ascontiguousarray(v.reshape(3, -1))
+
+    def _dims(self):
+        nz, ny, nx = self.shape
+        return nx, ny, nz
+
+    def init(self, C: np.ndarray) -> np.ndarray:
+        C = np.ascontiguousarray(C, np.float64).reshape(-1)
+        g = np.zeros((self.q,) + tuple(self.shape))
+        _check(lib().olb_oracle_ade_init(self.descriptor, *self._dims(), _p(C), _p(self._vf), _p(self._vu),
+                                         _p(g)), "ade_init")
+        return g
+
+    def step(self, g: np.ndarray, n: int = 1) -> np.ndarray:
+        if g.dtype != np.float64 or not g.flags.c_contiguous:
+            raise ValueError("g must be C-contiguous float64 [q, nz, ny, nx]")
+        _check(lib().olb_oracle_ade_step(self.descriptor, *self._dims(), float(self.tau), _p(self._vf),
+                                         _p(self._vu), _p(g), int(n)), "ade_step")
+        return g
+
+    def density(self, g: np.ndarray) -> np.ndarray:
+        C = np.zeros(tuple(self.shape))
+        _check(lib().olb_oracle_ade_density(self.descriptor, *self._dims(), _p(np.ascontiguousarray(g)), _p(C)),
+               "ade_density")
+        return C
 
 
 if __name__ == "__main__":  # pragma: no cover
