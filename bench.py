@@ -265,6 +265,27 @@ def variants(olb, torch):
             "MLUPS": round(fluid / ms / 1e3, 1), "bytes_per_update": b,
             "roofline_frac": round(fluid * b / (ms * 1e-3) / 1e9 / peak, 4)}
         lat.close()
+    # advection-diffusion, D3Q7 256^3 FP32, uniform velocity (7 x 4 x 2 = 56 B per update)
+    try:
+        n = 256
+        a = olb.AdeLattice(olb.D3Q7, (n, n, n), "f32")
+        a.set_tau(0.8)
+        a.set_velocity((0.02, -0.01, 0.015))
+        a.init(torch.ones(n ** 3, dtype=torch.float64, device="cuda"))
+        a.step(10)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(a.stream)
+        a.step(100)
+        ev[1].record(a.stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / 100
+        out["ade_d3q7_256_f32"] = {
+            "MLUPS": round(n ** 3 / ms / 1e3, 1), "bytes_per_update": 56,
+            "roofline_frac": round(n ** 3 * 56 / (ms * 1e-3) / 1e9 / peak, 4)}
+        a.close()
+    except Exception as e:  # an extra row: report, do not lose the bench line
+        out["ade_d3q7_256_f32"] = {"error": str(e)[:200]}
     # 3D Taylor-Green vortex 512^3, periodic (no wall cells)
     n = 512
     for dtype in ("f32", "f16"):

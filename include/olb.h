@@ -46,7 +46,9 @@ extern "C" {
 
 typedef struct olb_lattice* olb_handle;
 
-typedef enum { OLB_D2Q9 = 0, OLB_D3Q19 = 1 } olb_descriptor;
+/* D2Q9 and D3Q19: the fluid lattices (olb_lattice_create).  D2Q5 and D3Q7: the
+ * advection-diffusion lattices (olb_ade_create). */
+typedef enum { OLB_D2Q9 = 0, OLB_D3Q19 = 1, OLB_D2Q5 = 2, OLB_D3Q7 = 3 } olb_descriptor;
 
 /* Storage type of the populations on the GPU.  F64 and F32 store f_i - w_i and
  * compute in the same precision; the *_SHIFTED types store f_i - w_i in 16 bits
@@ -260,6 +262,38 @@ int olb_counters(olb_handle h, int64_t* time, int64_t* kernel_launches);
 int olb_statistics_noalloc(olb_descriptor d, int nx, int ny, int nz, const double* f,
                            const uint8_t* material, const double* force, double* out,
                            void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Advection-diffusion of a passive scalar (section "Advection--Diffusion
+ * Equation"): BGK on D2Q5 / D3Q7 towards the first-order equilibrium
+ *     g^eq_i = w_i C (1 + c_i . v / cs2),   C = sum_i g_i,
+ * diffusivity mu = cs2 (tau - 1/2); D2Q5: w = 1/3 (rest), 1/6, cs2 = 1/3; D3Q7:
+ * w = 1/4, 1/8, cs2 = 1/4 (the guide names these descriptors without printing
+ * their tables; the tables follow from sum w = 1 and sum w c_a c_b = cs2 delta).
+ * Every axis is periodic.  The velocity v is prescribed (uniform or per cell).
+ * The handle keeps the canonical state g(t) in two buffers of q x cells values
+ * (F64 or F32), obtained through the olb_set_allocator provider.  Calls queue
+ * work on the handle's stream (olb_ade_set_stream, default stream 0).
+ * --------------------------------------------------------------------------- */
+typedef struct olb_ade* olb_ade_handle;
+
+/* descriptor OLB_D2Q5 (nz = 1) or OLB_D3Q7; dtype OLB_F64 or OLB_F32; tau = 1 and
+ * v = 0 until set.  Errors: OLB_ERR_ARG, OLB_ERR_OOM. */
+int olb_ade_create(int descriptor, int nx, int ny, int nz, int dtype, olb_ade_handle* out);
+int olb_ade_destroy(olb_ade_handle h);
+int olb_ade_set_stream(olb_ade_handle h, void* cuda_stream);
+/* Relaxation time, tau > 1/2 (mu = cs2 (tau - 1/2)).  Errors: OLB_ERR_ARG. */
+int olb_ade_set_tau(olb_ade_handle h, double tau);
+/* Advection velocity: uniform v[3] (host), or per cell v_field double [3][cells]
+ * (host or device, copied during the call; takes precedence when both are given).
+ * The z component is ignored on D2Q5.  Errors: OLB_ERR_ARG (both NULL, non-finite). */
+int olb_ade_set_velocity(olb_ade_handle h, const double v[3], const double* v_field);
+/* g = g^eq(C, v) from C double [cells] (host or device). */
+int olb_ade_init(olb_ade_handle h, const double* C);
+/* n collide-and-stream steps. */
+int olb_ade_step(olb_ade_handle h, int64_t n);
+/* C = sum_i g_i into double [cells] (host: synchronises; device: queued). */
+int olb_ade_density(olb_ade_handle h, double* C);
 
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* olb_last_error(void);

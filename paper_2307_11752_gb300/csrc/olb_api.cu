@@ -1028,4 +1028,167 @@ int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t K, const doubl
   return adjoint_sweep(h, n_steps, K, seed, 1.0, loss, dL_dgamma, dL_dtau);
 }
 
+// ---------------------------------------------------------------------------------
+// Advection-diffusion lattice
+// ---------------------------------------------------------------------------------
+}  // extern "C"
+
+struct olb_ade {
+  int q = 0, dtype = 0;
+  int nx = 0, ny = 0, nz = 0;
+  int64_t ncell = 0;
+  cudaStream_t stream = nullptr;
+  DevBuf buf[2], vfield, stage;
+  int cur = 0;
+  double tau = 1.0;
+  double vu[3] = {0.0, 0.0, 0.0};
+  bool has_vfield = false;
+  size_t elem() const { return dtype == OLB_F64 ? sizeof(double) : sizeof(float); }
+  size_t state_bytes() const { return (size_t)q * ncell * elem(); }
+  AdeHost host() const {
+    AdeHost a;
+    a.q = q;
+    a.f64 = dtype == OLB_F64;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.ncell = ncell;
+    a.omega = 1.0 / tau;
+    for (int k = 0; k < 3; ++k) a.vu[k] = vu[k];
+    a.vf = has_vfield ? static_cast<const double*>(vfield.p) : nullptr;
+    a.stream = stream;
+    return a;
+  }
+};
+
+namespace {
+
+int ade_check(olb_ade_handle h) { return h ? OLB_OK : fail(OLB_ERR_ARG, "null advection-diffusion handle"); }
+
+// Device view of `bytes` bytes at p (copied into `tmp` when p is host memory).
+int ade_input(olb_ade_handle h, const void* p, size_t bytes, DevBuf& tmp, const void** out) {
+  if (is_device_pointer(p)) {
+    *out = p;
+    return OLB_OK;
+  }
+  int rc = tmp.reserve(bytes);
+  if (rc) return rc;
+  OLB_CUDA(cudaMemcpyAsync(tmp.p, p, bytes, cudaMemcpyHostToDevice, h->stream), "staging copy");
+  *out = tmp.p;
+  return OLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int olb_ade_create(int descriptor, int nx, int ny, int nz, int dtype, olb_ade_handle* out) {
+  if (!out) return fail(OLB_ERR_ARG, "null output handle");
+  *out = nullptr;
+  if (descriptor != OLB_D2Q5 && descriptor != OLB_D3Q7) return fail(OLB_ERR_ARG, "descriptor must be D2Q5 or D3Q7");
+  if (dtype != OLB_F64 && dtype != OLB_F32) return fail(OLB_ERR_ARG, "advection-diffusion storage is F64 or F32");
+  if (nx < 1 || ny < 1 || nz < 1) return fail(OLB_ERR_ARG, "lattice extents must be >= 1");
+  if (descriptor == OLB_D2Q5 && nz != 1) return fail(OLB_ERR_ARG, "D2Q5 needs nz == 1");
+  const int64_t cells = (int64_t)nx * ny * nz;
+  if (cells > ((int64_t)1 << 31) / 8) return fail(OLB_ERR_ARG, "lattice too large (%lld cells)", (long long)cells);
+  olb_ade* h = new olb_ade();
+  h->q = descriptor == OLB_D2Q5 ? 5 : 7;
+  h->dtype = dtype;
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->ncell = cells;
+  int rc;
+  if ((rc = h->buf[0].reserve(h->state_bytes())) || (rc = h->buf[1].reserve(h->state_bytes()))) {
+    std::string msg = g_err;
+    delete h;
+    g_err = msg;
+    return rc;
+  }
+  *out = h;
+  return OLB_OK;
+}
+
+int olb_ade_destroy(olb_ade_handle h) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+  return OLB_OK;
+}
+
+int olb_ade_set_stream(olb_ade_handle h, void* stream) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return OLB_OK;
+}
+
+int olb_ade_set_tau(olb_ade_handle h, double tau) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(OLB_ERR_ARG, "tau must be > 1/2 (got %g)", tau);
+  h->tau = tau;
+  return OLB_OK;
+}
+
+int olb_ade_set_velocity(olb_ade_handle h, const double v[3], const double* v_field) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  if (!v && !v_field) return fail(OLB_ERR_ARG, "no velocity given");
+  if (v) {
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(v[a])) return fail(OLB_ERR_ARG, "non-finite velocity");
+  }
+  if (v_field) {
+    const size_t bytes = 3 * (size_t)h->ncell * sizeof(double);
+    if ((rc = h->vfield.reserve(bytes))) return rc;
+    OLB_CUDA(cudaMemcpyAsync(h->vfield.p, v_field, bytes, cudaMemcpyDefault, h->stream), "velocity copy");
+    OLB_CUDA(cudaStreamSynchronize(h->stream), "velocity sync");
+    h->has_vfield = true;
+  } else {
+    for (int a = 0; a < 3; ++a) h->vu[a] = (h->q == 5 && a == 2) ? 0.0 : v[a];
+    h->has_vfield = false;
+  }
+  return OLB_OK;
+}
+
+int olb_ade_init(olb_ade_handle h, const double* C) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  if (!C) return fail(OLB_ERR_ARG, "null scalar field");
+  const void* dc = nullptr;
+  if ((rc = ade_input(h, C, (size_t)h->ncell * sizeof(double), h->stage, &dc))) return rc;
+  OLB_CUDA(ade_init(h->host(), static_cast<const double*>(dc), h->buf[h->cur].p), "advection-diffusion init");
+  return OLB_OK;
+}
+
+int olb_ade_step(olb_ade_handle h, int64_t n) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  if (n < 0) return fail(OLB_ERR_ARG, "negative step count");
+  const AdeHost a = h->host();
+  for (int64_t s = 0; s < n; ++s) {
+    OLB_CUDA(ade_step(a, h->buf[h->cur].p, h->buf[1 - h->cur].p), "advection-diffusion step");
+    h->cur = 1 - h->cur;
+  }
+  return OLB_OK;
+}
+
+int olb_ade_density(olb_ade_handle h, double* C) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  if (!C) return fail(OLB_ERR_ARG, "null output");
+  const size_t bytes = (size_t)h->ncell * sizeof(double);
+  if (is_device_pointer(C)) {
+    OLB_CUDA(ade_density(h->host(), h->buf[h->cur].p, C), "advection-diffusion density");
+    return OLB_OK;
+  }
+  if ((rc = h->stage.reserve(bytes))) return rc;
+  OLB_CUDA(ade_density(h->host(), h->buf[h->cur].p, static_cast<double*>(h->stage.p)), "advection-diffusion density");
+  OLB_CUDA(cudaMemcpyAsync(C, h->stage.p, bytes, cudaMemcpyDeviceToHost, h->stream), "density copy");
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "density sync");
+  return OLB_OK;
+}
+
 }  // extern "C"

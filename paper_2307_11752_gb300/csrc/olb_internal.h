@@ -106,6 +106,21 @@ const KernelTable* table_d3q19_f32();
 const KernelTable* table_d3q19_f16();
 const KernelTable* table_d3q19_bf16();
 
+// Advection-diffusion lattice (D2Q5: q = 5, D3Q7: q = 7), kernels in olb_ade.cu.
+struct AdeHost {
+  int q;
+  bool f64;               // storage and arithmetic in double (else float)
+  int nx, ny, nz;
+  int64_t ncell;
+  double omega;
+  double vu[3];           // uniform advection velocity (used when vf is null)
+  const double* vf;       // per-cell velocity [3][ncell] or nullptr
+  cudaStream_t stream;
+};
+cudaError_t ade_step(const AdeHost& h, const void* src, void* dst);
+cudaError_t ade_init(const AdeHost& h, const double* C, void* g);
+cudaError_t ade_density(const AdeHost& h, const void* g, double* C);
+
 // Record the message returned by olb_last_error() on this thread; returns code.
 int set_error(int code, const char* msg);
 

@@ -55,6 +55,14 @@ SIGNATURES = {
     "olb_diagnostics": [_P, _P],
     "olb_adjoint_run": [_P, _I64, _I64, _P, _P, _P, _P],
     "olb_adjoint_run_misfit": [_P, _I64, _I64, _P, _P, _P, _P, _P],
+    "olb_ade_create": [_I, _I, _I, _I, _I, _P],
+    "olb_ade_destroy": [_P],
+    "olb_ade_set_stream": [_P, _P],
+    "olb_ade_set_tau": [_P, _D],
+    "olb_ade_set_velocity": [_P, _P, _P],
+    "olb_ade_init": [_P, _P],
+    "olb_ade_step": [_P, _I64],
+    "olb_ade_density": [_P, _P],
     "olb_synchronize": [_P],
     "olb_counters": [_P, _P, _P],
     "olb_statistics_noalloc": [_I, _I, _I, _I, _P, _P, _P, _P, _P],
@@ -351,6 +359,68 @@ class Lattice:
         t, k = ctypes.c_int64(), ctypes.c_int64()
         _call("olb_counters", self.handle, ctypes.byref(t), ctypes.byref(k))
         return t.value, k.value
+
+
+# --------------------------------------------------------------------------------------
+# Advection-diffusion lattice (D2Q5 / D3Q7)
+# --------------------------------------------------------------------------------------
+D2Q5, D3Q7 = 2, 3
+
+
+class AdeLattice:
+    """A passive scalar on a periodic D2Q5 / D3Q7 lattice (``olb_ade_*``): BGK towards
+    the first-order equilibrium, advected by a prescribed velocity."""
+
+    def __init__(self, descriptor: int, shape, dtype: str = "f64", stream=None):
+        import torch
+
+        nx, ny, nz = shape
+        h = ctypes.c_void_p()
+        _call("olb_ade_create", int(descriptor), int(nx), int(ny), int(nz), DTYPES[dtype], ctypes.byref(h))
+        self.handle = h
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.cells = nx * ny * nz
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        _call("olb_ade_set_stream", self.handle, ctypes.c_void_p(self.stream.cuda_stream))
+
+    def close(self):
+        if self.handle is not None:
+            load().olb_ade_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass
+
+    def set_tau(self, tau: float):
+        _call("olb_ade_set_tau", self.handle, float(tau))
+
+    def set_velocity(self, v=None, field=None):
+        vv = None if v is None else (ctypes.c_double * 3)(*[float(a) for a in (list(v) + [0, 0, 0])[:3]])
+        if field is not None:
+            _check_array(field, "float64", 3 * self.cells, "velocity field")
+        pf, kf = _ptr(field)
+        _call("olb_ade_set_velocity", self.handle, vv, pf)
+
+    def init(self, C):
+        _check_array(C, "float64", self.cells, "C")
+        p, k = _ptr(C)
+        _call("olb_ade_init", self.handle, p)
+
+    def step(self, n: int = 1):
+        _call("olb_ade_step", self.handle, int(n))
+
+    def density(self, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device="cuda")
+        _check_array(out, "float64", self.cells, "C")
+        p, k = _ptr(out)
+        _call("olb_ade_density", self.handle, p)
+        return out
 
 
 # --------------------------------------------------------------------------------------
