@@ -520,6 +520,21 @@ def experiment_domain_id(torch, olb, dtype="f32", iterations=20):
     return out
 
 
+def reduce_over_ranks(torch, world: int, maxes, sums, device):
+    """Whole-job figures of a multi-rank run: the max over ranks of each value in
+    `maxes` (times) and the sum over ranks of each value in `sums` (counts), through
+    the default process group on `device`.  On one rank both lists come back as given."""
+    if world <= 1:
+        return [float(v) for v in maxes], [float(v) for v in sums]
+    import torch.distributed as dist
+
+    a = torch.tensor([float(v) for v in maxes], dtype=torch.float64, device=device)
+    s = torch.tensor([float(v) for v in sums], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return a.tolist(), s.tolist()
+
+
 def run_ours(args):
     import torch
 
@@ -540,22 +555,22 @@ def run_ours(args):
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         ms, launches, stats = time_device(torch, lat, noise, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clocks = clk.summary()
     kernel_ms = time_step_kernel(torch, lat, 500)
     lat.close()
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    e2e_sec, h2d, d2h = e2e_run(olb, torch, m, max(1, min(args.steps, 3)))
+    # whole job: slowest rank's times, every rank's units and launches
+    (ms_max, e2e_max), (launches_all,) = reduce_over_ranks(torch, world, [ms, e2e_sec], [launches], "cuda")
     units = fluid * LBM_STEPS * args.steps * world
     value = units / (ms_max * 1e-3) / 1e6
     peak, peak_kind = measured_peak_gbs()
     bytes_per_launch = fluid * 152
     achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
     traffic = profiled_traffic("d3q19_f32_pull", fluid)
-    e2e_sec, h2d, d2h = e2e_run(olb, torch, m, max(1, min(args.steps, 3)))
-    e2e_units = fluid * LBM_STEPS * max(1, min(args.steps, 3))
+    e2e_units = fluid * LBM_STEPS * max(1, min(args.steps, 3)) * world
     extra = variants(olb, torch) if (args.variants and rank == 0) else None
     if world > 1:
         dist.barrier()
@@ -575,9 +590,9 @@ def run_ours(args):
                      "traffic": None if traffic is None else round(traffic),
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": round(kernel_ms, 5)},
-        "e2e": {"value": round(e2e_units / e2e_sec / 1e6, 2), "unit": "MLUPS",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
+        "e2e": {"value": round(e2e_units / e2e_max / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d * world, "d2h_bytes_per_step": d2h * world},
+        "gpu_launches": int(launches_all),
         "build": olb.build_info(),
         "clocks": clocks,
         "statistics_last_step": {"mass": stats[0], "max_u": stats[5], "nonfinite": stats[6]},
