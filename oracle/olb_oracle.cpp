@@ -133,6 +133,7 @@ typedef struct {
   double force[3];         // uniform body force density F (Guo)
   const double* gamma;     // per-cell porosity in [0,1] or NULL (gamma = 1)
   double magic;            // TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2), omega+ = 1/tau
+  const double* force_field;  // per-cell force density [3][n], or NULL (the uniform force above)
 } olb_oracle_lattice;
 
 // Objective of the adjoint, evaluated on the state after the last step.
@@ -202,22 +203,24 @@ void equilibrium(const Desc& D, T rho, const T u[3], T* feq) {
   }
 }
 
-// Moments of one cell: rho = sum f, j = sum c f, u = (j + F/2)/rho.
-template <class T>
-void moments(const Desc& D, const T* f, const double F[3], T& rho, T j[3], T u[3]) {
+// Moments of one cell: rho = sum f, j = sum c f, u = (j + F/2)/rho.  F is a double
+// or, for forward-mode derivatives with respect to the force, a T.
+template <class T, class TF>
+void moments(const Desc& D, const T* f, const TF F[3], T& rho, T j[3], T u[3]) {
   rho = T(0.0);
   j[0] = j[1] = j[2] = T(0.0);
   for (int i = 0; i < D.q; ++i) {
     rho += f[i];
     for (int a = 0; a < 3; ++a) j[a] += double(D.c[i][a]) * f[i];
   }
-  for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
+  for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * T(F[a])) / rho;
 }
 
 // One BGK collision of one cell with Guo forcing and porosity scaling.
 //   f*_i = (1 - omega) f_i + omega f^eq_i(rho, gamma u) + (1 - omega/2) S_i(gamma u)
-template <class T>
-void collide_cell(const Desc& D, const T* f, T gamma, T omega, const double F[3], T* fs) {
+template <class T, class TF>
+void collide_cell(const Desc& D, const T* f, T gamma, T omega, const TF Fin[3], T* fs) {
+  const T F[3] = {T(Fin[0]), T(Fin[1]), T(Fin[2])};
   T rho, j[3], u[3];
   moments(D, f, F, rho, j, u);
   T up[3] = {gamma * u[0], gamma * u[1], gamma * u[2]};
@@ -225,9 +228,9 @@ void collide_cell(const Desc& D, const T* f, T gamma, T omega, const double F[3]
   equilibrium(D, rho, up, feq);
   T uF = up[0] * F[0] + up[1] * F[1] + up[2] * F[2];
   for (int i = 0; i < D.q; ++i) {
-    double cF = D.c[i][0] * F[0] + D.c[i][1] * F[1] + D.c[i][2] * F[2];
+    T cF = D.c[i][0] * F[0] + D.c[i][1] * F[1] + D.c[i][2] * F[2];
     T cu = D.c[i][0] * up[0] + D.c[i][1] * up[1] + D.c[i][2] * up[2];
-    T S = D.w[i] * ((T(cF) - uF) / D.cs2 + cu * cF / (D.cs2 * D.cs2));
+    T S = D.w[i] * ((cF - uF) / D.cs2 + cu * cF / (D.cs2 * D.cs2));
     fs[i] = (T(1.0) - omega) * f[i] + omega * feq[i] + (T(1.0) - 0.5 * omega) * S;
   }
 }
@@ -240,8 +243,9 @@ void collide_cell(const Desc& D, const T* f, T gamma, T omega, const double F[3]
 //              + (1 - omega+/2) S+_i + (1 - omega-/2) S-_i,
 // omega+ = 1/tau sets the viscosity, omega- follows from the magic parameter
 // Lambda = (1/omega+ - 1/2)(1/omega- - 1/2).  omega- = omega+ is BGK.
-template <class T>
-void collide_cell_trt(const Desc& D, const T* f, T gamma, T omega_p, T omega_m, const double F[3], T* fs) {
+template <class T, class TF>
+void collide_cell_trt(const Desc& D, const T* f, T gamma, T omega_p, T omega_m, const TF Fin[3], T* fs) {
+  const T F[3] = {T(Fin[0]), T(Fin[1]), T(Fin[2])};
   T rho, j[3], u[3];
   moments(D, f, F, rho, j, u);
   T up[3] = {gamma * u[0], gamma * u[1], gamma * u[2]};
@@ -249,9 +253,9 @@ void collide_cell_trt(const Desc& D, const T* f, T gamma, T omega_p, T omega_m, 
   equilibrium(D, rho, up, feq);
   T uF = up[0] * F[0] + up[1] * F[1] + up[2] * F[2];
   for (int i = 0; i < D.q; ++i) {
-    double cF = D.c[i][0] * F[0] + D.c[i][1] * F[1] + D.c[i][2] * F[2];
+    T cF = D.c[i][0] * F[0] + D.c[i][1] * F[1] + D.c[i][2] * F[2];
     T cu = D.c[i][0] * up[0] + D.c[i][1] * up[1] + D.c[i][2] * up[2];
-    S[i] = D.w[i] * ((T(cF) - uF) / D.cs2 + cu * cF / (D.cs2 * D.cs2));
+    S[i] = D.w[i] * ((cF - uF) / D.cs2 + cu * cF / (D.cs2 * D.cs2));
   }
   for (int i = 0; i < D.q; ++i) {
     const int o = D.opp[i];
@@ -269,6 +273,14 @@ T omega_minus(T omega_p, double magic) {
   return T(1.0) / (T(magic) / (T(1.0) / omega_p - T(0.5)) + T(0.5));
 }
 
+// Force density at cell c: the T field Ff ([3][n], forward-mode runs), else the
+// lattice's per-cell field, else its uniform force.
+template <class T>
+void cell_force(const olb_oracle_lattice* L, const T* Ff, int64_t n, int64_t c, T F[3]) {
+  for (int a = 0; a < 3; ++a)
+    F[a] = Ff ? Ff[a * n + c] : T(L->force_field ? L->force_field[a * n + c] : L->force[a]);
+}
+
 template <class T>
 T gamma_at(const olb_oracle_lattice* L, const T* gamma, int64_t c) {
   if (gamma) return gamma[c];
@@ -278,7 +290,8 @@ T gamma_at(const olb_oracle_lattice* L, const T* gamma, int64_t c) {
 
 // Collision of every fluid cell: fs = C(f); non-fluid cells copied unchanged.
 template <class T>
-void collide_field(const olb_oracle_lattice* L, const T* f, const T* gamma, T omega, T* fs) {
+void collide_field(const olb_oracle_lattice* L, const T* f, const T* gamma, T omega, T* fs,
+                   const T* Ff = nullptr) {
   Geo g(L);
   const Desc& D = *g.D;
   const bool trt = L->collision == 1;
@@ -288,10 +301,12 @@ void collide_field(const olb_oracle_lattice* L, const T* f, const T* gamma, T om
     T fc[19], fsc[19];
     for (int i = 0; i < D.q; ++i) fc[i] = f[i * g.n + c];
     if (g.mat[c] == 1) {
+      T F[3];
+      cell_force(L, Ff, g.n, c, F);
       if (trt)
-        collide_cell_trt(D, fc, gamma_at(L, gamma, c), omega, om_m, L->force, fsc);
+        collide_cell_trt(D, fc, gamma_at(L, gamma, c), omega, om_m, F, fsc);
       else
-        collide_cell(D, fc, gamma_at(L, gamma, c), omega, L->force, fsc);
+        collide_cell(D, fc, gamma_at(L, gamma, c), omega, F, fsc);
     } else {
       for (int i = 0; i < D.q; ++i) fsc[i] = fc[i];
     }
@@ -337,11 +352,12 @@ void stream_field(const olb_oracle_lattice* L, const T* fs, const T* fpre, T* fo
 }
 
 template <class T>
-void step_field(const olb_oracle_lattice* L, T* f, const T* gamma, T omega, int64_t nsteps) {
+void step_field(const olb_oracle_lattice* L, T* f, const T* gamma, T omega, int64_t nsteps,
+                const T* Ff = nullptr) {
   Geo g(L);
   std::vector<T> fs((size_t)g.D->q * g.n), fo((size_t)g.D->q * g.n);
   for (int64_t s = 0; s < nsteps; ++s) {
-    collide_field(L, f, gamma, omega, fs.data());
+    collide_field(L, f, gamma, omega, fs.data(), Ff);
     stream_field(L, fs.data(), f, fo.data());
     std::memcpy((void*)f, (const void*)fo.data(), sizeof(T) * fo.size());
   }
@@ -385,14 +401,16 @@ bool objective_cells(const Geo& g, const olb_oracle_objective* obj, std::vector<
 
 template <class T>
 T loss_of(const olb_oracle_lattice* L, const T* f, const std::vector<int64_t>& cells,
-          const olb_oracle_objective* obj) {
+          const olb_oracle_objective* obj, const T* Ff = nullptr) {
   Geo g(L);
   const Desc& D = *g.D;
   T acc = T(0.0);
   for (int64_t c : cells) {
     T fc[19], rho, j[3], u[3];
     for (int i = 0; i < D.q; ++i) fc[i] = f[i * g.n + c];
-    moments(D, fc, L->force, rho, j, u);
+    T F[3];
+    cell_force(L, Ff, g.n, c, F);
+    moments(D, fc, F, rho, j, u);
     if (obj->kind == 1) {
       for (int a = 0; a < D.d; ++a) {
         T e = u[a] - T(obj->u_target[a * g.n + c]);
@@ -412,9 +430,13 @@ T loss_of(const olb_oracle_lattice* L, const T* f, const std::vector<int64_t>& c
 //   TRT (trt = true):  the even parts relax at omega, the odd parts at omega_m, and
 //   omega_m depends on omega through the magic parameter (d omega_m / d omega =
 //   domega_m), so d f*/d omega includes that chain.
+//   dF[k][b] (optional) = d f*_k / d F_b of the cell's force density: through
+//   u = (j + F/2)/rho (d u'_a / d F_b = gamma delta_ab / (2 rho)) and the explicit F of
+//   the Guo source.
 void collision_jacobian(const Desc& D, const double* f, double gamma, double omega,
                         const double F[3], double J[19][19], double dg[19], double dw[19],
-                        bool trt = false, double omega_m = 0.0, double domega_m = 0.0) {
+                        bool trt = false, double omega_m = 0.0, double domega_m = 0.0,
+                        double (*dF)[3] = nullptr) {
   double rho, j[3], u[3];
   moments(D, f, F, rho, j, u);
   double up[3] = {gamma * u[0], gamma * u[1], gamma * u[2]};
@@ -422,8 +444,9 @@ void collision_jacobian(const Desc& D, const double* f, double gamma, double ome
   equilibrium(D, rho, up, feq);
   double uF = up[0] * F[0] + up[1] * F[1] + up[2] * F[2];
   double cs2 = D.cs2;
-  // d feq_k / d f_i, d S_k / d f_i, and their gamma derivatives; S_k itself
-  double Ep[19][19], Sp[19][19], Eg[19], Sg[19], S[19];
+  // d feq_k / d f_i, d S_k / d f_i, and their gamma derivatives; S_k itself; the
+  // force derivatives of feq_k and S_k (EF, SF)
+  double Ep[19][19], Sp[19][19], Eg[19], Sg[19], S[19], EF[19][3], SF[19][3];
   for (int k = 0; k < D.q; ++k) {
     double cu = D.c[k][0] * up[0] + D.c[k][1] * up[1] + D.c[k][2] * up[2];
     double cF = D.c[k][0] * F[0] + D.c[k][1] * F[1] + D.c[k][2] * F[2];
@@ -447,6 +470,11 @@ void collision_jacobian(const Desc& D, const double* f, double gamma, double ome
     Eg[k] = dE_du[0] * u[0] + dE_du[1] * u[1] + dE_du[2] * u[2];
     Sg[k] = dS_du[0] * u[0] + dS_du[1] * u[1] + dS_du[2] * u[2];
     S[k] = D.w[k] * ((cF - uF) / cs2 + cu * cF / (cs2 * cs2));
+    for (int b = 0; b < 3; ++b) {
+      const double du = gamma / (2.0 * rho);  // d u'_b / d F_b
+      EF[k][b] = dE_du[b] * du;
+      SF[k][b] = dS_du[b] * du + D.w[k] * ((D.c[k][b] - up[b]) / cs2 + cu * D.c[k][b] / (cs2 * cs2));
+    }
   }
   if (!trt) {
     for (int k = 0; k < D.q; ++k) {
@@ -454,6 +482,8 @@ void collision_jacobian(const Desc& D, const double* f, double gamma, double ome
         J[k][i] = (k == i ? 1.0 - omega : 0.0) + omega * Ep[k][i] + (1.0 - 0.5 * omega) * Sp[k][i];
       dg[k] = omega * Eg[k] + (1.0 - 0.5 * omega) * Sg[k];
       dw[k] = -f[k] + feq[k] - 0.5 * S[k];
+      if (dF)
+        for (int b = 0; b < 3; ++b) dF[k][b] = omega * EF[k][b] + (1.0 - 0.5 * omega) * SF[k][b];
     }
     return;
   }
@@ -474,6 +504,10 @@ void collision_jacobian(const Desc& D, const double* f, double gamma, double ome
     double d_even = -(0.5 * (f[k] + f[o]) - 0.5 * (feq[k] + feq[o])) - 0.25 * (S[k] + S[o]);
     double d_odd = -(0.5 * (f[k] - f[o]) - 0.5 * (feq[k] - feq[o])) - 0.25 * (S[k] - S[o]);
     dw[k] = d_even + d_odd * domega_m;
+    if (dF)
+      for (int b = 0; b < 3; ++b)
+        dF[k][b] = omega * 0.5 * (EF[k][b] + EF[o][b]) + omega_m * 0.5 * (EF[k][b] - EF[o][b]) +
+                   gp * 0.5 * (SF[k][b] + SF[o][b]) + gm * 0.5 * (SF[k][b] - SF[o][b]);
   }
 }
 
@@ -518,7 +552,7 @@ void stream_transpose(const olb_oracle_lattice* L, const double* lam, double* la
 // post-collision state); accumulates gradients with respect to gamma (per cell)
 // and omega (scalar).
 void collide_transpose(const olb_oracle_lattice* L, const double* f, const double* lams,
-                       double* lam, double* dgamma, double* domega) {
+                       double* lam, double* dgamma, double* domega, double* dforce = nullptr) {
   Geo g(L);
   const Desc& D = *g.D;
   double omega = 1.0 / L->tau;
@@ -535,10 +569,17 @@ void collide_transpose(const olb_oracle_lattice* L, const double* f, const doubl
       for (int i = 0; i < D.q; ++i) lam[i * g.n + c] = 0.0;
       continue;
     }
-    double fc[19], J[19][19], dg[19], dwk[19];
+    double fc[19], J[19][19], dg[19], dwk[19], dF[19][3], Fc[3];
     for (int i = 0; i < D.q; ++i) fc[i] = f[i * g.n + c];
     double gam = L->gamma ? L->gamma[c] : 1.0;
-    collision_jacobian(D, fc, gam, omega, L->force, J, dg, dwk, trt, omega_m, domega_m);
+    cell_force<double>(L, nullptr, g.n, c, Fc);
+    collision_jacobian(D, fc, gam, omega, Fc, J, dg, dwk, trt, omega_m, domega_m, dF);
+    if (dforce)
+      for (int b = 0; b < 3; ++b) {
+        double v = 0.0;
+        for (int k = 0; k < D.q; ++k) v += dF[k][b] * lams[k * g.n + c];
+        dforce[b * g.n + c] += v;
+      }
     double gsum = 0.0, wsum = 0.0;
     for (int i = 0; i < D.q; ++i) {
       double v = 0.0;
@@ -557,6 +598,20 @@ void collide_transpose(const olb_oracle_lattice* L, const double* f, const doubl
     for (int64_t c = 0; c < g.n; ++c) s.add(dw_cell[c]);
     *domega += s.get();
   }
+}
+
+// Force field as dual numbers: the lattice's force (value) with direction dir
+// ([3][n]); an empty vector when dir is NULL (the plain double force is used).
+std::vector<Dual> dual_force(const olb_oracle_lattice* L, int64_t n, const double* dir) {
+  std::vector<Dual> Ff;
+  if (!dir) return Ff;
+  Ff.resize(3 * (size_t)n);
+  for (int64_t c = 0; c < n; ++c) {
+    double F[3];
+    cell_force<double>(L, nullptr, n, c, F);
+    for (int a = 0; a < 3; ++a) Ff[a * n + c] = Dual(F[a], dir[a * n + c]);
+  }
+  return Ff;
 }
 
 }  // namespace
@@ -656,7 +711,9 @@ int olb_oracle_moments(const olb_oracle_lattice* L, const double* f, double* rho
     }
     double fc[19], r, j[3], uc[3];
     for (int i = 0; i < D.q; ++i) fc[i] = f[i * g.n + c];
-    moments(D, fc, L->force, r, j, uc);
+    double Fc[3];
+    cell_force<double>(L, nullptr, g.n, c, Fc);
+    moments(D, fc, Fc, r, j, uc);
     rho[c] = r;
     for (int a = 0; a < 3; ++a) u[a * g.n + c] = uc[a];
   }
@@ -681,7 +738,9 @@ int olb_oracle_diagnostics(const olb_oracle_lattice* L, const double* f, double*
       if (!std::isfinite(fc[i])) finite = false;
     }
     if (!finite) { bad += 1.0; continue; }
-    moments(D, fc, L->force, r, j, u);
+    double Fc[3];
+    cell_force<double>(L, nullptr, g.n, c, Fc);
+    moments(D, fc, Fc, r, j, u);
     m.add(r);
     jx.add(j[0]); jy.add(j[1]); jz.add(j[2]);
     double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -708,7 +767,7 @@ int olb_oracle_loss(const olb_oracle_lattice* L, const double* f,
 // in the direction (dgamma_dir per cell, dtau_dir): dloss = dL/dgamma . v + dL/dtau * s.
 int olb_oracle_tangent(const olb_oracle_lattice* L, const double* f0, int64_t nsteps,
                        const olb_oracle_objective* obj, const double* dgamma_dir,
-                       double dtau_dir, double* loss, double* dloss) {
+                       double dtau_dir, double* loss, double* dloss, const double* dforce_dir) {
   if (!valid(L) || nsteps < 0) return -1;
   Geo g(L);
   const Desc& D = *g.D;
@@ -720,8 +779,10 @@ int olb_oracle_tangent(const olb_oracle_lattice* L, const double* f0, int64_t ns
     gam[c] = Dual(L->gamma ? L->gamma[c] : 1.0, dgamma_dir ? dgamma_dir[c] : 0.0);
   // omega = 1/tau, d omega = -d tau / tau^2
   Dual omega = Dual(1.0, 0.0) / Dual(L->tau, dtau_dir);
-  step_field<Dual>(L, f.data(), gam.data(), omega, nsteps);
-  Dual Lv = loss_of<Dual>(L, f.data(), cells, obj);
+  std::vector<Dual> Ff = dual_force(L, g.n, dforce_dir);
+  const Dual* Fp = Ff.empty() ? nullptr : Ff.data();
+  step_field<Dual>(L, f.data(), gam.data(), omega, nsteps, Fp);
+  Dual Lv = loss_of<Dual>(L, f.data(), cells, obj, Fp);
   *loss = Lv.v;
   *dloss = Lv.d;
   return 0;
@@ -730,7 +791,7 @@ int olb_oracle_tangent(const olb_oracle_lattice* L, const double* f0, int64_t ns
 // Jacobian-vector products of the single sub-operators, for the transpose pins:
 //   dfs = (dC/df) df + (dC/dgamma) dgamma + (dC/dtau) dtau   at state f
 int olb_oracle_collide_tangent(const olb_oracle_lattice* L, const double* f, const double* df,
-                               const double* dgamma, double dtau, double* dfs) {
+                               const double* dgamma, double dtau, double* dfs, const double* dforce) {
   if (!valid(L)) return -1;
   Geo g(L);
   const Desc& D = *g.D;
@@ -739,17 +800,19 @@ int olb_oracle_collide_tangent(const olb_oracle_lattice* L, const double* f, con
   for (int64_t c = 0; c < g.n; ++c)
     gam[c] = Dual(L->gamma ? L->gamma[c] : 1.0, dgamma ? dgamma[c] : 0.0);
   Dual omega = Dual(1.0, 0.0) / Dual(L->tau, dtau);
-  collide_field<Dual>(L, fd.data(), gam.data(), omega, fs.data());
+  std::vector<Dual> Ff = dual_force(L, g.n, dforce);
+  collide_field<Dual>(L, fd.data(), gam.data(), omega, fs.data(), Ff.empty() ? nullptr : Ff.data());
   for (size_t k = 0; k < fs.size(); ++k) dfs[k] = fs[k].d;
   return 0;
 }
 
 //   lam = (dC/df)^T lams;  dgamma += (dC/dgamma)^T lams;  dtau += (dC/dtau)^T lams
 int olb_oracle_collide_adjoint(const olb_oracle_lattice* L, const double* f,
-                               const double* lams, double* lam, double* dgamma, double* dtau) {
+                               const double* lams, double* lam, double* dgamma, double* dtau,
+                               double* dforce) {
   if (!valid(L)) return -1;
   double domega = 0.0;
-  collide_transpose(L, f, lams, lam, dgamma, &domega);
+  collide_transpose(L, f, lams, lam, dgamma, &domega, dforce);
   if (dtau) *dtau += -domega / (L->tau * L->tau);
   return 0;
 }
@@ -772,7 +835,7 @@ int olb_oracle_stream_adjoint(const olb_oracle_lattice* L, const double* lam, do
 // lambda0 (optional, q x n) receives dL/df^0.
 int olb_oracle_adjoint(const olb_oracle_lattice* L, const double* f0, int64_t nsteps,
                        const olb_oracle_objective* obj, double* loss, double* dgamma,
-                       double* dtau, double* lambda0) {
+                       double* dtau, double* lambda0, double* dforce) {
   if (!valid(L) || nsteps < 0) return -1;
   Geo g(L);
   const Desc& D = *g.D;
@@ -791,10 +854,14 @@ int olb_oracle_adjoint(const olb_oracle_lattice* L, const double* f0, int64_t ns
   //   plane mean of u_a:  (1/M) (c_ia - u_a) / rho
   //   velocity misfit:    sum_a (u_a - u*_a) (c_ia - u_a) / rho
   std::vector<double> lam(qn, 0.0), lams(qn), lamn(qn), direct(g.n);
+  if (dforce)
+    for (int64_t k = 0; k < 3 * g.n; ++k) dforce[k] = 0.0;
   for (int64_t c : cells) {
     double fc[19], r, j[3], u[3];
     for (int i = 0; i < D.q; ++i) fc[i] = fN[i * g.n + c];
-    moments(D, fc, L->force, r, j, u);
+    double Fc[3];
+    cell_force<double>(L, nullptr, g.n, c, Fc);
+    moments(D, fc, Fc, r, j, u);
     for (int i = 0; i < D.q; ++i) {
       double v = 0.0;
       if (obj->kind == 1) {
@@ -805,12 +872,20 @@ int olb_oracle_adjoint(const olb_oracle_lattice* L, const double* f0, int64_t ns
       }
       lam[i * g.n + c] = v;
     }
+    // the objective's own dependence on the force, through u = (j + F/2)/rho
+    if (dforce) {
+      if (obj->kind == 1) {
+        for (int a = 0; a < D.d; ++a) dforce[a * g.n + c] += (u[a] - obj->u_target[a * g.n + c]) / (2.0 * r);
+      } else {
+        dforce[obj->component * g.n + c] += 1.0 / (2.0 * r * double(cells.size()));
+      }
+    }
   }
   std::vector<double> gg(g.n, 0.0);
   double domega = 0.0;
   for (int64_t s = nsteps - 1; s >= 0; --s) {
     stream_transpose(L, lam.data(), lams.data(), direct.data());
-    collide_transpose(L, states[s].data(), lams.data(), lamn.data(), gg.data(), &domega);
+    collide_transpose(L, states[s].data(), lams.data(), lamn.data(), gg.data(), &domega, dforce);
     for (int64_t c = 0; c < g.n; ++c) {
       if (g.mat[c] != 1) continue;
       for (int i = 0; i < D.q; ++i) lamn[i * g.n + c] += direct[c];

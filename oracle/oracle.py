@@ -48,7 +48,8 @@ class _Lattice(ctypes.Structure):
                 ("periodic", ctypes.c_uint32), ("collision", ctypes.c_int32),
                 ("material", ctypes.c_void_p), ("wall_u", ctypes.c_void_p),
                 ("tau", ctypes.c_double), ("force", ctypes.c_double * 3),
-                ("gamma", ctypes.c_void_p), ("magic", ctypes.c_double)]
+                ("gamma", ctypes.c_void_p), ("magic", ctypes.c_double),
+                ("force_field", ctypes.c_void_p)]
 
 
 class _Objective(ctypes.Structure):
@@ -101,11 +102,11 @@ def lib():
             "olb_oracle_moments": [P, P, P, P],
             "olb_oracle_diagnostics": [P, P, P],
             "olb_oracle_loss": [P, P, P, P],
-            "olb_oracle_tangent": [P, P, I64, P, P, D, P, P],
-            "olb_oracle_collide_tangent": [P, P, P, P, D, P],
-            "olb_oracle_collide_adjoint": [P, P, P, P, P, P],
+            "olb_oracle_tangent": [P, P, I64, P, P, D, P, P, P],
+            "olb_oracle_collide_tangent": [P, P, P, P, D, P, P],
+            "olb_oracle_collide_adjoint": [P, P, P, P, P, P, P],
             "olb_oracle_stream_adjoint": [P, P, P, P],
-            "olb_oracle_adjoint": [P, P, I64, P, P, P, P, P],
+            "olb_oracle_adjoint": [P, P, I64, P, P, P, P, P, P],
             "olb_oracle_ade_descriptor": [ctypes.c_int, P, P, P, P, P, P],
             "olb_oracle_ade_init": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P],
             "olb_oracle_ade_step": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, P, P, P, I64],
@@ -185,6 +186,7 @@ class Lattice:
     wall_u: np.ndarray = field(default_factory=lambda: np.zeros((256, 3)))
     collision: int = BGK
     magic: float = 0.25
+    force_field: Optional[np.ndarray] = None  # per-cell force density [3, nz, ny, nx]
 
     def __post_init__(self):
         self.material = np.ascontiguousarray(self.material, np.uint8)
@@ -193,6 +195,8 @@ class Lattice:
         self.wall_u = np.ascontiguousarray(self.wall_u, np.float64).reshape(256, 3)
         if self.gamma is not None:
             self.gamma = np.ascontiguousarray(self.gamma, np.float64).reshape(self.material.shape)
+        if self.force_field is not None:
+            self.force_field = np.ascontiguousarray(self.force_field, np.float64).reshape((3,) + self.material.shape)
         self.q = descriptor(self.descriptor)[1]
 
     @property
@@ -208,7 +212,7 @@ class Lattice:
         F = (ctypes.c_double * 3)(*[float(v) for v in (list(self.force) + [0, 0, 0])[:3]])
         self._keep = _Lattice(self.descriptor, nx, ny, nz, self.periodic, int(self.collision),
                               self.material.ctypes.data, self.wall_u.ctypes.data,
-                              float(self.tau), F, _p(self.gamma), float(self.magic))
+                              float(self.tau), F, _p(self.gamma), float(self.magic), _p(self.force_field))
         return self._keep
 
     def _f(self, f: np.ndarray) -> np.ndarray:
@@ -263,30 +267,36 @@ class Lattice:
                                      ctypes.byref(out)), "loss")
         return out.value
 
-    def tangent(self, f0: np.ndarray, n: int, objective, dgamma=None, dtau: float = 0.0):
+    def tangent(self, f0: np.ndarray, n: int, objective, dgamma=None, dtau: float = 0.0, dforce=None):
+        """(loss, directional derivative) along (dgamma per cell, dtau, dforce [3, nz, ny, nx])."""
         loss, dl = ctypes.c_double(), ctypes.c_double()
         obj, keep = _objective(objective, self.shape)
         dg = None if dgamma is None else np.ascontiguousarray(dgamma, np.float64)
+        dF = None if dforce is None else np.ascontiguousarray(dforce, np.float64).reshape((3,) + self.shape)
         _check(lib().olb_oracle_tangent(ctypes.byref(self._c()), _p(self._f(f0)), int(n),
                                         ctypes.byref(obj), _p(dg), float(dtau),
-                                        ctypes.byref(loss), ctypes.byref(dl)), "tangent")
+                                        ctypes.byref(loss), ctypes.byref(dl), _p(dF)), "tangent")
         return loss.value, dl.value
 
-    def collide_tangent(self, f, df, dgamma=None, dtau=0.0):
+    def collide_tangent(self, f, df, dgamma=None, dtau=0.0, dforce=None):
         out = np.zeros_like(self._f(f))
         dg = None if dgamma is None else np.ascontiguousarray(dgamma, np.float64)
+        dF = None if dforce is None else np.ascontiguousarray(dforce, np.float64).reshape((3,) + self.shape)
         _check(lib().olb_oracle_collide_tangent(ctypes.byref(self._c()), _p(f),
                                                 _p(self._f(np.ascontiguousarray(df))), _p(dg),
-                                                float(dtau), _p(out)), "collide_tangent")
+                                                float(dtau), _p(out), _p(dF)), "collide_tangent")
         return out
 
-    def collide_adjoint(self, f, lams):
+    def collide_adjoint(self, f, lams, want_dforce: bool = False):
         lam = np.zeros_like(self._f(f))
         dg = np.zeros(self.shape)
         dt = ctypes.c_double(0.0)
+        dF = np.zeros((3,) + self.shape) if want_dforce else None
         _check(lib().olb_oracle_collide_adjoint(ctypes.byref(self._c()), _p(f),
                                                 _p(self._f(np.ascontiguousarray(lams))), _p(lam),
-                                                _p(dg), ctypes.byref(dt)), "collide_adjoint")
+                                                _p(dg), ctypes.byref(dt), _p(dF)), "collide_adjoint")
+        if want_dforce:
+            return lam, dg, dt.value, dF
         return lam, dg, dt.value
 
     def stream_adjoint(self, lam):
@@ -296,18 +306,25 @@ class Lattice:
                                                _p(direct)), "stream_adjoint")
         return lams, direct
 
-    def adjoint(self, f0: np.ndarray, n: int, objective, want_lambda0: bool = False):
-        """(loss, dL/dgamma [nz,ny,nx], dL/dtau[, dL/df0]) of the objective after n steps."""
+    def adjoint(self, f0: np.ndarray, n: int, objective, want_lambda0: bool = False,
+                want_dforce: bool = False):
+        """(loss, dL/dgamma [nz,ny,nx], dL/dtau[, dL/df0][, dL/dF [3,nz,ny,nx]]) of the
+        objective after n steps; dL/dF is the gradient with respect to the force density
+        of every cell."""
         loss, dtau = ctypes.c_double(), ctypes.c_double()
         dg = np.zeros(self.shape)
         lam0 = self.zeros() if want_lambda0 else None
+        dF = np.zeros((3,) + self.shape) if want_dforce else None
         obj, keep = _objective(objective, self.shape)
         _check(lib().olb_oracle_adjoint(ctypes.byref(self._c()), _p(self._f(f0)), int(n),
                                         ctypes.byref(obj), ctypes.byref(loss), _p(dg),
-                                        ctypes.byref(dtau), _p(lam0)), "adjoint")
+                                        ctypes.byref(dtau), _p(lam0), _p(dF)), "adjoint")
+        out = (loss.value, dg, dtau.value)
         if want_lambda0:
-            return loss.value, dg, dtau.value, lam0
-        return loss.value, dg, dtau.value
+            out = out + (lam0,)
+        if want_dforce:
+            out = out + (dF,)
+        return out
 
 
 # ------------------------------------------------------------------------------------
