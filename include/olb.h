@@ -14,7 +14,11 @@
  * a per-cell porosity that scales the equilibrium velocity (section "Porous
  * Media Model").  olb_adjoint_run returns the gradient of a plane-averaged
  * velocity with respect to the porosity field and tau (the adjoint approach of
- * section "Derivative Computation", taken here as the exact discrete adjoint).
+ * section "Derivative Computation", taken here as the exact discrete adjoint);
+ * olb_adjoint_run_misfit does the same for the velocity misfit of the guide's
+ * optimisation examples.  olb_set_trt selects the TRT collision instead of BGK
+ * (forward only).  The olb_ade_* calls run a separate advection-diffusion
+ * lattice (D2Q5 / D3Q7, section "Advection--Diffusion Equation").
  *
  * Conventions shared by every call
  * --------------------------------

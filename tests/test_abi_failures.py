@@ -55,3 +55,23 @@ def test_arguments_rejected_before_any_device_call(lib):
     assert lib.olb_step(None, 1) == -1
     assert lib.olb_lattice_destroy(None) == -1
     assert lib.olb_set_allocator(ctypes.c_void_p(1), None, None) == -1  # alloc without free
+
+
+def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
+    """Argument errors of the TRT, misfit and advection-diffusion calls are reported
+    before any device work."""
+    from paper_2307_11752_gb300 import olb
+
+    h = ctypes.c_void_p()
+    assert lib.olb_set_trt(None, 0.8, 0.25) == -1
+    assert lib.olb_adjoint_run_misfit(None, 5, 2, None, None, None, None, None) == -1
+    assert lib.olb_ade_create(olb.D2Q9, 8, 8, 1, olb.F32, ctypes.byref(h)) == -1
+    assert "D2Q5 or D3Q7" in lib.olb_last_error().decode()
+    assert lib.olb_ade_create(olb.D2Q5, 8, 8, 2, olb.F32, ctypes.byref(h)) == -1
+    assert lib.olb_ade_create(olb.D3Q7, 8, 8, 8, olb.F16_SHIFTED, ctypes.byref(h)) == -1
+    assert lib.olb_ade_create(olb.D3Q7, 0, 8, 8, olb.F32, ctypes.byref(h)) == -1
+    assert lib.olb_ade_create(olb.D3Q7, 8, 8, 8, olb.F32, None) == -1
+    calls = {"olb_ade_destroy": (None,), "olb_ade_step": (None, 1), "olb_ade_set_tau": (None, 0.8),
+             "olb_ade_init": (None, None), "olb_ade_density": (None, None)}
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == -1, name
