@@ -964,6 +964,10 @@ bool ade_valid(const AdeDesc* D, int nx, int ny, int nz) {
 
 extern "C" {
 
+int olb_oracle_ade_step_bc(int d, int nx, int ny, int nz, unsigned periodic, const uint8_t* material,
+                           const double* wall_C, double tau, const double* v, const double* vu, double* g,
+                           int64_t nsteps);
+
 // Table of D2Q5 (d = 0) or D3Q7 (d = 1): dim, q, c[q][3], opposite[q], w[q], cs2.
 int olb_oracle_ade_descriptor(int d, int* dim, int* q, int* c, int* opp, double* w, double* cs2) {
   const AdeDesc* D = ade_descriptor(d);
@@ -997,14 +1001,36 @@ int olb_oracle_ade_init(int d, int nx, int ny, int nz, const double* C, const do
 // nsteps BGK collide-and-stream steps on a fully periodic lattice, in place.
 int olb_oracle_ade_step(int d, int nx, int ny, int nz, double tau, const double* v,
                         const double* vu, double* g, int64_t nsteps) {
+  return olb_oracle_ade_step_bc(d, nx, ny, nz, 7u, nullptr, nullptr, tau, v, vu, g, nsteps);
+}
+
+// As olb_oracle_ade_step with boundaries.  material (cells, NULL = all 1):
+//   1 = bulk cell (collided and streamed),
+//   0 = no-flux wall: a link into it bounces back, g_opp(i)(x) = g*_i(x),
+//   2..255 = Dirichlet cell of value wall_C[m] (the guide's constant-temperature
+//       boundary, named without its scheme -- read as anti-bounce-back):
+//       g_opp(i)(x) = -g*_i(x) + 2 w_i C_w, which fixes C_w at the link's midpoint.
+// Links that leave the domain along a non-periodic axis (bit a of `periodic`
+// clear) bounce back like a no-flux wall.  Non-bulk cells keep their values.
+int olb_oracle_ade_step_bc(int d, int nx, int ny, int nz, unsigned periodic, const uint8_t* material,
+                           const double* wall_C, double tau, const double* v, const double* vu, double* g,
+                           int64_t nsteps) {
   const AdeDesc* D = ade_descriptor(d);
   if (!ade_valid(D, nx, ny, nz) || !(tau > 0.5) || !g || nsteps < 0) return -1;
   const int64_t n = (int64_t)nx * ny * nz;
+  if (material && !wall_C)
+    for (int64_t c = 0; c < n; ++c)
+      if (material[c] >= 2) return -1;
   const double omega = 1.0 / tau;
+  const int e[3] = {nx, ny, nz};
   std::vector<double> gs((size_t)D->q * n);
   for (int64_t s = 0; s < nsteps; ++s) {
 #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < n; ++c) {
+      if (material && material[c] != 1) {
+        for (int i = 0; i < D->q; ++i) gs[i * n + c] = g[i * n + c];
+        continue;
+      }
       double C = 0.0;
       for (int i = 0; i < D->q; ++i) C += g[i * n + c];
       double vc[3], geq[7];
@@ -1017,11 +1043,25 @@ int olb_oracle_ade_step(int d, int nx, int ny, int nz, double tau, const double*
       for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
           const int64_t c = ((int64_t)z * ny + y) * nx + x;
+          if (material && material[c] != 1) continue;
           for (int i = 0; i < D->q; ++i) {
-            const int tx = (x + D->c[i][0] + nx) % nx;
-            const int ty = (y + D->c[i][1] + ny) % ny;
-            const int tz = (z + D->c[i][2] + nz) % nz;
-            g[i * n + ((int64_t)tz * ny + ty) * nx + tx] = gs[i * n + c];
+            int p[3] = {x + D->c[i][0], y + D->c[i][1], z + D->c[i][2]};
+            bool inside = true;
+            for (int a = 0; a < 3; ++a) {
+              if (p[a] < 0 || p[a] >= e[a]) {
+                if (periodic & (1u << a)) p[a] = (p[a] + e[a]) % e[a];
+                else inside = false;
+              }
+            }
+            const int64_t t = inside ? ((int64_t)p[2] * ny + p[1]) * nx + p[0] : -1;
+            const int m = (t < 0) ? 0 : (material ? material[t] : 1);
+            if (m == 1) {
+              g[i * n + t] = gs[i * n + c];
+            } else if (m >= 2) {
+              g[D->opp[i] * n + c] = -gs[i * n + c] + 2.0 * D->w[i] * wall_C[m];
+            } else {
+              g[D->opp[i] * n + c] = gs[i * n + c];
+            }
           }
         }
   }

@@ -111,6 +111,8 @@ def lib():
             "olb_oracle_ade_init": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P],
             "olb_oracle_ade_step": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, P, P, P, I64],
             "olb_oracle_ade_density": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P],
+            "olb_oracle_ade_step_bc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint, P, P, D,
+                                       P, P, P, I64],
         }
         for name, args in sig.items():
             fn = getattr(_lib, name)
@@ -351,9 +353,21 @@ class AdeLattice:
     shape: tuple
     tau: float
     v: object = (0.0, 0.0, 0.0)
+    # boundaries (None: every cell bulk, every axis periodic): material uint8 [nz, ny, nx]
+    # with 1 bulk, 0 no-flux wall, 2..255 Dirichlet cell of value wall_C[m]
+    material: Optional[np.ndarray] = None
+    wall_C: Optional[np.ndarray] = None
+    periodic: int = 7
 
     def __post_init__(self):
         self.q = ade_descriptor(self.descriptor)[1]
+        if self.material is not None:
+            self.material = np.ascontiguousarray(self.material, np.uint8).reshape(tuple(self.shape))
+        if self.wall_C is not None:
+            wc = np.zeros(256)
+            src = np.asarray(self.wall_C, np.float64).reshape(-1)
+            wc[:src.size] = src
+            self.wall_C = wc
         v = np.asarray(self.v, np.float64)
         if v.size == 3:
             self._vu, self._vf = np.ascontiguousarray(v.reshape(3)), None
@@ -374,8 +388,13 @@ class AdeLattice:
     def step(self, g: np.ndarray, n: int = 1) -> np.ndarray:
         if g.dtype != np.float64 or not g.flags.c_contiguous:
             raise ValueError("g must be C-contiguous float64 [q, nz, ny, nx]")
-        _check(lib().olb_oracle_ade_step(self.descriptor, *self._dims(), float(self.tau), _p(self._vf),
-                                         _p(self._vu), _p(g), int(n)), "ade_step")
+        if self.material is None and self.periodic == 7:
+            _check(lib().olb_oracle_ade_step(self.descriptor, *self._dims(), float(self.tau), _p(self._vf),
+                                             _p(self._vu), _p(g), int(n)), "ade_step")
+        else:
+            _check(lib().olb_oracle_ade_step_bc(self.descriptor, *self._dims(), int(self.periodic),
+                                                _p(self.material), _p(self.wall_C), float(self.tau),
+                                                _p(self._vf), _p(self._vu), _p(g), int(n)), "ade_step_bc")
         return g
 
     def density(self, g: np.ndarray) -> np.ndarray:

@@ -127,3 +127,72 @@ def test_advection_diffusion_3d_second_order(oracle):
     errs = [_sine_run(oracle, 1, n, 0.8, 0.05, (0.5, 0.25, -0.3), 0.3, 3) for n in (12, 24, 48)]
     eoc = _eoc(errs)
     assert all(1.8 <= e <= 2.3 for e in eoc), (errs, eoc)
+
+
+# ---------------------------------------------------------------------------------
+# Boundaries: no-flux walls (bounce-back) and Dirichlet cells (the guide's constant-
+# temperature boundary, read as anti-bounce-back g_opp(i)(x) = -g*_i(x) + 2 w_i C_w).
+# ---------------------------------------------------------------------------------
+def _plates(d, n_par, ny, lo=2, hi=3):
+    shape = (1, ny, n_par) if d == 0 else (n_par, ny, n_par)
+    m = np.ones(shape, np.uint8)
+    m[:, 0, :] = lo
+    m[:, -1, :] = hi
+    return m
+
+
+@pytest.mark.parametrize("d,tau,v", [(0, 0.6, 0.0), (0, 1.0, 0.05), (0, 2.0, 0.0), (1, 0.8, 0.04)])
+def test_dirichlet_plates_give_the_exact_linear_profile(oracle, d, tau, v):
+    """Steady diffusion between two Dirichlet plates: C is the straight line through
+    C_lo and C_hi at the halfway walls y = 1/2 and y = ny - 3/2, whatever tau and a
+    velocity along the plates."""
+    ny = 12
+    m = _plates(d, 4, ny)
+    wall = np.zeros(256)
+    wall[2], wall[3] = 1.0, 2.0
+    lat = oracle.AdeLattice(d, m.shape, tau, (v, 0.0, 0.0), material=m, wall_C=wall,
+                            periodic=1 if d == 0 else 5)
+    g = lat.init(np.where(m == 1, 1.5, 0.0))
+    prev = None
+    for _ in range(400):
+        lat.step(g, 200)
+        C = lat.density(g)[0, 1:-1, 0]
+        if prev is not None and np.max(np.abs(C - prev)) < 1e-15:
+            break
+        prev = C
+    y = np.arange(1, ny - 1, dtype=float)
+    exact = 1.0 + (y - 0.5) / (ny - 2)
+    assert np.max(np.abs(C - exact)) <= 1e-12
+
+
+@pytest.mark.parametrize("d", [0, 1])
+def test_no_flux_walls_conserve_the_scalar(oracle, d):
+    shape = (1, 9, 11) if d == 0 else (6, 7, 8)
+    m = np.zeros(shape, np.uint8)
+    if d == 0:
+        m[0, 1:-1, 1:-1] = 1
+    else:
+        m[1:-1, 1:-1, 1:-1] = 1
+    lat = oracle.AdeLattice(d, shape, 0.7, (0.05, -0.02, 0.03 if d == 1 else 0.0), material=m, periodic=0)
+    C = np.where(m == 1, 1.0 + I.uniform(31, shape), 0.0)
+    g = lat.init(C)
+    bulk = m == 1
+    total = g[:, bulk].sum()
+    lat.step(g, 150)
+    assert abs(g[:, bulk].sum() - total) <= 1e-13 * total
+
+
+def test_domain_edges_act_as_no_flux_walls(oracle):
+    """A non-periodic edge and an explicit layer of no-flux cells give the same bulk."""
+    C = 1.0 + I.uniform(32, (1, 8, 10))
+    a = oracle.AdeLattice(0, (1, 8, 10), 0.8, (0.03, 0.02, 0.0), periodic=0)
+    ga = a.init(C)
+    a.step(ga, 60)
+    m = np.zeros((1, 10, 12), np.uint8)
+    m[0, 1:-1, 1:-1] = 1
+    Cb = np.zeros((1, 10, 12))
+    Cb[0, 1:-1, 1:-1] = C[0]
+    b = oracle.AdeLattice(0, (1, 10, 12), 0.8, (0.03, 0.02, 0.0), material=m, periodic=0)
+    gb = b.init(Cb)
+    b.step(gb, 60)
+    assert np.array_equal(a.density(ga)[0], b.density(gb)[0, 1:-1, 1:-1])
