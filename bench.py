@@ -624,9 +624,11 @@ def _threads():
     return int(n) if n else len(os.sched_getaffinity(0))
 
 
-def cpu_baseline(seconds: float = 12.0):
+def cpu_baseline(seconds: float = 12.0, single_thread_seconds: float = 4.0):
     """The oracle as it stands on the host cores, on a bounded sample of the
-    workload: as many LBM steps of the 128^3 cavity as fit in ~`seconds`."""
+    workload: as many LBM steps of the 128^3 cavity as fit in ~`seconds`; with
+    `single_thread_seconds` > 0 also on one thread (a child process with
+    OMP_NUM_THREADS=1, since the thread count is fixed when the oracle loads)."""
     lat, f, fluid = _oracle_cavity()
     t = time.perf_counter()
     lat.step(f, 1)
@@ -635,9 +637,19 @@ def cpu_baseline(seconds: float = 12.0):
     t = time.perf_counter()
     lat.step(f, n)
     sec = time.perf_counter() - t
-    return {"value": round(fluid * n / sec / 1e6, 3), "unit": "MLUPS", "cores": _threads(),
-            "kind": "oracle",
-            "sample": f"{n} of the {LBM_STEPS} FP64 steps of the {N_SIDE}^3 cavity (after 1 warm-up step)"}
+    out = {"value": round(fluid * n / sec / 1e6, 3), "unit": "MLUPS", "cores": _threads(),
+           "kind": "oracle",
+           "sample": f"{n} of the {LBM_STEPS} FP64 steps of the {N_SIDE}^3 cavity (after 1 warm-up step)"}
+    if single_thread_seconds > 0:
+        code = ("import json, bench; print(json.dumps(bench.cpu_baseline(%r, 0)))" % float(single_thread_seconds))
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                           env=dict(os.environ, OMP_NUM_THREADS="1"), timeout=600)
+        if r.returncode == 0:
+            one_thread = json.loads(r.stdout.strip().splitlines()[-1])
+            out["single_thread"] = {k: one_thread[k] for k in ("value", "unit", "cores", "sample")}
+        else:
+            out["single_thread"] = {"error": r.stderr.strip().splitlines()[-1][:200] if r.stderr else "failed"}
+    return out
 
 
 def run_reference(args):
