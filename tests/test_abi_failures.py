@@ -75,3 +75,18 @@ def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
              "olb_ade_init": (None, None), "olb_ade_density": (None, None)}
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == -1, name
+
+
+def test_oversized_lattices_are_rejected_before_allocation(lib):
+    """The largest lattices the 32-bit cell index supports: beyond them creation
+    fails with OLB_ERR_ARG and allocates nothing (no GPU needed to see it)."""
+    from paper_2307_11752_gb300 import olb
+
+    h = ctypes.c_void_p()
+    assert lib.olb_lattice_create(olb.D3Q19, 2048, 1024, 1024, olb.F32, ctypes.byref(h)) == -1
+    assert "2^31" in lib.olb_last_error().decode()
+    assert lib.olb_lattice_create(olb.D3Q19, 1, 1, 70000, olb.F32, ctypes.byref(h)) == -1
+    assert "nz" in lib.olb_last_error().decode()
+    assert lib.olb_ade_create(olb.D3Q7, 1024, 1024, 512, olb.F32, ctypes.byref(h)) == -1
+    assert "too large" in lib.olb_last_error().decode()
+    assert h.value is None
