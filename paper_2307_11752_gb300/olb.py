@@ -5,9 +5,12 @@ the CUDA kernels of libolb.so.  PyTorch supplies device memory (the library
 allocates through torch's caching allocator) and the CUDA stream.  There is no
 CPU fallback: if libolb.so is missing or no GPU is present, the calls raise.
 
-The functions ``olb_*`` mirror the C names one to one; :class:`Lattice` is a
-thin object wrapper and :func:`plane_velocity_loss` puts ``olb_adjoint_run``
-behind ``torch.autograd``.
+The functions ``olb_*`` mirror the C names one to one.
+  :class:`Lattice`               the fluid lattice (BGK or TRT collision, pull or AA)
+  :func:`plane_velocity_loss`    ``olb_adjoint_run`` behind ``torch.autograd``
+  :func:`velocity_misfit_loss`   ``olb_adjoint_run_misfit`` behind ``torch.autograd``
+  :class:`AdeLattice`            the advection-diffusion lattice (D2Q5 / D3Q7)
+The porosity identification driver built on these is ``paper_2307_11752_gb300.opti``.
 """
 from __future__ import annotations
 
