@@ -26,10 +26,14 @@
  *    are structure-of-arrays [q][cells] in the canonical, unshifted form:
  *    pre-collision populations f(t) in double precision.  Velocity arrays are
  *    [3][cells] (the z component is 0 on D2Q9).
- *  - Array arguments may point to device memory or to host memory (pinned or
- *    pageable); the library asks the driver which one it is and stages host data
- *    through a device buffer.  The caller owns every array; the library only reads
- *    or writes it during the call (no pointer is kept).
+ *  - Array arguments may point to device memory of the current device (or managed
+ *    memory) or to host memory (pinned or pageable); the library asks the driver
+ *    which one it is and stages host data through a device buffer.  Device memory
+ *    of another GPU is refused with OLB_ERR_ARG.  The caller owns every array; the
+ *    library only reads or writes it during the call (no pointer is kept).
+ *  - A handle lives on the device that was current when it was created; every
+ *    call on it except the destroy call needs that device current (OLB_ERR_ARG
+ *    otherwise).
  *  - Work is queued on the handle's CUDA stream (olb_set_stream; default: the
  *    legacy default stream).  Calls that return data through host pointers
  *    synchronise that stream before returning; the others are asynchronous.
@@ -260,9 +264,12 @@ int olb_counters(olb_handle h, int64_t* time, int64_t* kernel_launches);
  * on a device share the array, so calls that overlap on the GPU (on different
  * streams) race; order them on one stream.  Each call overwrites every partial sum
  * it reads, so no clearing is needed between calls.
+ * The lookup is keyed on the device's current context, so after a device reset
+ * the next call looks the address up again.
  * Errors: OLB_ERR_ARG for more than 16,777,216 cells (65,536 blocks of 256 cells,
  * the capacity of the fixed array), a bad descriptor or size, null f/out, or
- * arrays that are not device memory; OLB_ERR_CUDA for a failed launch. */
+ * arrays that are not device memory of the current device (host memory is not
+ * staged: staging would allocate); OLB_ERR_CUDA for a failed launch. */
 int olb_statistics_noalloc(olb_descriptor d, int nx, int ny, int nz, const double* f,
                            const uint8_t* material, const double* force, double* out,
                            void* cuda_stream);

@@ -120,14 +120,28 @@ const KernelTable* table_for(int d, int t) {
   return tables[d][t]();
 }
 
-bool is_device_pointer(const void* p) {
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+// Makes `device` current for the scope and restores the previous device.
+struct DeviceScope {
+  int prev = -1, dev;
+  explicit DeviceScope(int device) : dev(device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    if (prev != dev) cudaSetDevice(dev);
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  ~DeviceScope() {
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  }
+};
+
+// OLB_OK with *dev = (p is memory the current device can use), or OLB_ERR_ARG
+// when p is device memory of another GPU.
+int locate(const void* p, bool* dev, const char* what) {
+  const MemKind k = mem_kind(p);
+  if (k == MEM_OTHER_DEVICE) return fail(OLB_ERR_ARG, "%s is device memory of another GPU than the current one", what);
+  *dev = k == MEM_DEVICE;
+  return OLB_OK;
 }
 
 // Cell classes and link masks from the material numbers (same tables as the
@@ -221,6 +235,20 @@ void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, u
 
 }  // namespace
 
+MemKind olb::mem_kind(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return MEM_HOST;
+  }
+  int dev = -1;
+  if (a.type == cudaMemoryTypeDevice && cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return MEM_OTHER_DEVICE;
+  }
+  return classify_memory(a.type, a.device, dev);
+}
+
 int olb::set_error(int code, const char* msg) {
   g_err = msg ? msg : "";
   return code;
@@ -230,6 +258,7 @@ int olb::set_error(int code, const char* msg) {
 // Handle
 // ---------------------------------------------------------------------------------
 struct olb_lattice {
+  int device = 0;  // the CUDA device the handle's buffers live on
   int desc = 0, dtype = 0, q = 0, dim = 0;
   int nx = 0, ny = 0, nz = 0, ncell = 0, pitch = 0;
   const KernelTable* kt = nullptr;
@@ -355,10 +384,20 @@ cudaError_t reduce_partials(const double* partials, int64_t rows, double* out, c
 
 namespace {
 
+// The handle's device must be the current one: its kernels run on the current
+// device and address the handle's buffers.
+int check_device(int device) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != device) return fail(OLB_ERR_ARG, "handle belongs to device %d but device %d is current", device, cur);
+  return OLB_OK;
+}
+
 int check(olb_handle h) {
   if (!h) return fail(OLB_ERR_ARG, "null handle");
   g_err.clear();
-  return OLB_OK;
+  return check_device(h->device);
 }
 
 int launched(olb_handle h, cudaError_t e, const char* what) {
@@ -370,11 +409,14 @@ int launched(olb_handle h, cudaError_t e, const char* what) {
 // Device view of a caller array of `bytes` bytes for reading.  Host memory is
 // copied into h->stage (or `tmp`) on the handle's stream.
 int input_view(olb_handle h, const void* p, size_t bytes, DevBuf& tmp, const void** out) {
-  if (is_device_pointer(p)) {
+  bool dev = false;
+  int rc = locate(p, &dev, "input array");
+  if (rc) return rc;
+  if (dev) {
     *out = p;
     return OLB_OK;
   }
-  int rc = tmp.reserve(bytes);
+  rc = tmp.reserve(bytes);
   if (rc) return rc;
   OLB_CUDA(cudaMemcpyAsync(tmp.p, p, bytes, cudaMemcpyHostToDevice, h->stream), "staging copy");
   *out = tmp.p;
@@ -456,7 +498,10 @@ int deliver_stats(olb_handle h, double* out) {
   OLB_CUDA(cudaMemcpyAsync(r, h->out8.p, sizeof(r), cudaMemcpyDeviceToHost, h->stream), "stats copy");
   OLB_CUDA(cudaStreamSynchronize(h->stream), "stats sync");
   double o[7] = {r[7] + r[0], r[1], r[2], r[3], r[4], r[5], r[6]};
-  if (is_device_pointer(out)) {
+  bool dev = false;
+  int rc = locate(out, &dev, "statistics output");
+  if (rc) return rc;
+  if (dev) {
     OLB_CUDA(cudaMemcpyAsync(out, o, sizeof(o), cudaMemcpyHostToDevice, h->stream), "stats out");
     OLB_CUDA(cudaStreamSynchronize(h->stream), "stats sync");
   } else {
@@ -627,7 +672,13 @@ int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, ol
   const int64_t cells = (int64_t)nx * ny * nz;
   if (cells > 2147483647LL - 4096) return fail(OLB_ERR_ARG, "more than 2^31 - 4097 cells");
   if (nz > 65535) return fail(OLB_ERR_ARG, "nz > 65535");
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {  // no usable device: the first allocation reports it
+    cudaGetLastError();
+    device = 0;
+  }
   olb_lattice* h = new olb_lattice();
+  h->device = device;
   h->desc = (int)d;
   h->dtype = (int)t;
   h->kt = kt;
@@ -665,6 +716,8 @@ int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, ol
 
 int olb_lattice_destroy(olb_handle h) {
   if (!h) return fail(OLB_ERR_ARG, "null handle");
+  // release on the handle's own device, whichever device is current
+  DeviceScope on(h->device);
   cudaStreamSynchronize(h->stream);
   delete h;
   g_err.clear();
@@ -699,7 +752,9 @@ int olb_set_material(olb_handle h, const uint8_t* material, unsigned periodic_ma
     return fail(OLB_ERR_ARG, "z cannot be periodic on D2Q9");
   const size_t n = (size_t)h->ncell;
   std::vector<uint8_t> m(n);
-  if (is_device_pointer(material)) {
+  bool dev = false;
+  if ((rc = locate(material, &dev, "material array"))) return rc;
+  if (dev) {
     OLB_CUDA(cudaMemcpy(m.data(), material, n, cudaMemcpyDeviceToHost), "material read");
   } else {
     std::memcpy(m.data(), material, n);
@@ -882,7 +937,8 @@ int olb_get_populations(olb_handle h, double* f) {
   if (rc) return rc;
   if (!f) return fail(OLB_ERR_ARG, "null output");
   const size_t bytes = (size_t)h->q * h->ncell * sizeof(double);
-  const bool dev = is_device_pointer(f);
+  bool dev = false;
+  if ((rc = locate(f, &dev, "population output"))) return rc;
   DevBuf tmp;
   if (!dev && (rc = tmp.reserve(bytes))) return rc;
   double* d = dev ? f : static_cast<double*>(tmp.p);
@@ -924,8 +980,9 @@ int olb_moments(olb_handle h, double* rho, double* u) {
   if (rc) return rc;
   if (!rho && !u) return OLB_OK;
   const size_t nr = (size_t)h->ncell * sizeof(double), nu = 3 * nr;
-  const bool dr = rho ? is_device_pointer(rho) : true;
-  const bool du = u ? is_device_pointer(u) : true;
+  bool dr = true, du = true;
+  if (rho && (rc = locate(rho, &dr, "density output"))) return rc;
+  if (u && (rc = locate(u, &du, "velocity output"))) return rc;
   DevBuf t1, t2;
   if (rho && !dr && (rc = t1.reserve(nr))) return rc;
   if (u && !du && (rc = t2.reserve(nu))) return rc;
@@ -1034,6 +1091,7 @@ int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t K, const doubl
 }  // extern "C"
 
 struct olb_ade {
+  int device = 0;  // the CUDA device the handle's buffers live on
   int q = 0, dtype = 0;
   int nx = 0, ny = 0, nz = 0;
   int64_t ncell = 0;
@@ -1063,15 +1121,21 @@ struct olb_ade {
 
 namespace {
 
-int ade_check(olb_ade_handle h) { return h ? OLB_OK : fail(OLB_ERR_ARG, "null advection-diffusion handle"); }
+int ade_check(olb_ade_handle h) {
+  if (!h) return fail(OLB_ERR_ARG, "null advection-diffusion handle");
+  return check_device(h->device);
+}
 
 // Device view of `bytes` bytes at p (copied into `tmp` when p is host memory).
 int ade_input(olb_ade_handle h, const void* p, size_t bytes, DevBuf& tmp, const void** out) {
-  if (is_device_pointer(p)) {
+  bool dev = false;
+  int rc = locate(p, &dev, "input array");
+  if (rc) return rc;
+  if (dev) {
     *out = p;
     return OLB_OK;
   }
-  int rc = tmp.reserve(bytes);
+  rc = tmp.reserve(bytes);
   if (rc) return rc;
   OLB_CUDA(cudaMemcpyAsync(tmp.p, p, bytes, cudaMemcpyHostToDevice, h->stream), "staging copy");
   *out = tmp.p;
@@ -1091,7 +1155,13 @@ int olb_ade_create(int descriptor, int nx, int ny, int nz, int dtype, olb_ade_ha
   if (descriptor == OLB_D2Q5 && nz != 1) return fail(OLB_ERR_ARG, "D2Q5 needs nz == 1");
   const int64_t cells = (int64_t)nx * ny * nz;
   if (cells > ((int64_t)1 << 31) / 8) return fail(OLB_ERR_ARG, "lattice too large (%lld cells)", (long long)cells);
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {  // no usable device: the first allocation reports it
+    cudaGetLastError();
+    device = 0;
+  }
   olb_ade* h = new olb_ade();
+  h->device = device;
   h->q = descriptor == OLB_D2Q5 ? 5 : 7;
   h->dtype = dtype;
   h->nx = nx;
@@ -1110,8 +1180,8 @@ int olb_ade_create(int descriptor, int nx, int ny, int nz, int dtype, olb_ade_ha
 }
 
 int olb_ade_destroy(olb_ade_handle h) {
-  int rc = ade_check(h);
-  if (rc) return rc;
+  if (!h) return fail(OLB_ERR_ARG, "null advection-diffusion handle");
+  DeviceScope on(h->device);
   cudaStreamSynchronize(h->stream);
   delete h;
   return OLB_OK;
@@ -1180,7 +1250,9 @@ int olb_ade_density(olb_ade_handle h, double* C) {
   if (rc) return rc;
   if (!C) return fail(OLB_ERR_ARG, "null output");
   const size_t bytes = (size_t)h->ncell * sizeof(double);
-  if (is_device_pointer(C)) {
+  bool dev = false;
+  if ((rc = locate(C, &dev, "density output"))) return rc;
+  if (dev) {
     OLB_CUDA(ade_density(h->host(), h->buf[h->cur].p, C), "advection-diffusion density");
     return OLB_OK;
   }

@@ -121,6 +121,20 @@ cudaError_t ade_step(const AdeHost& h, const void* src, void* dst);
 cudaError_t ade_init(const AdeHost& h, const double* C, void* g);
 cudaError_t ade_density(const AdeHost& h, const void* g, double* C);
 
+// Where a caller's array lives, seen from the current device: host memory
+// (pageable or pinned), memory the current device can use (its own device
+// allocations, or managed memory), or device memory of another GPU (refused by
+// every entry point: the kernels would address it without peer access).
+enum MemKind { MEM_HOST = 0, MEM_DEVICE = 1, MEM_OTHER_DEVICE = 2 };
+MemKind mem_kind(const void* p);
+// The classification from the pointer's attributes (memory type, the device that
+// owns it) and the current device.
+inline MemKind classify_memory(cudaMemoryType type, int owner_device, int current_device) {
+  if (type == cudaMemoryTypeManaged) return MEM_DEVICE;
+  if (type != cudaMemoryTypeDevice) return MEM_HOST;
+  return owner_device == current_device ? MEM_DEVICE : MEM_OTHER_DEVICE;
+}
+
 // Record the message returned by olb_last_error() on this thread; returns code.
 int set_error(int code, const char* msg);
 

@@ -10,6 +10,8 @@
 // fixed array in the library's own device memory instead of a buffer it
 // allocates.  The array is a file-scope __device__ variable: every GPU that loads
 // the library holds it (4 MiB) until the process exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -28,21 +30,23 @@ constexpr int kMaxDevices = 64;
 // One row of 8 partial sums per block (see olb::block_reduce_row).
 static __device__ __align__(256) double g_partial_rows[kMaxBlocks * 8];
 
-// Device address of g_partial_rows for each device (host code may not use the
-// symbol itself: on the host it names a stand-in, not device memory).
+// Device address of g_partial_rows for each device, with the context it was
+// looked up in (host code may not use the symbol itself: on the host it names a
+// stand-in, not device memory).  A device reset destroys the context and the
+// module with it; the next call then sees another current context and looks the
+// address up again instead of using the stale one.
+struct RowsAddress {
+  CUcontext ctx = nullptr;
+  double* addr = nullptr;
+};
 std::mutex g_setup_mu;
-double* g_rows_addr[kMaxDevices] = {nullptr};
+RowsAddress g_rows[kMaxDevices];
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
 
 int static_fail(int code, const char* msg) { return olb::set_error(code, msg); }
 
-bool on_device(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// Memory the current device can address (its own allocations or managed memory).
+bool on_device(const void* p) { return olb::mem_kind(p) == olb::MEM_DEVICE; }
 
 // Statistics of a canonical (unshifted, FP64) population array: per-cell
 // contributions {rho - 1, j, |u|^2/2, |u|, non-finite, 1} over fluid cells,
@@ -100,24 +104,42 @@ __global__ void k_stats_finish(const double* __restrict__ rows, int nrows, doubl
   }
 }
 
-// Device address of the partial-sum array on the current device, looked up
-// once per device with that device current.
+// Device address of the partial-sum array on the current device, looked up with
+// that device current the first time the device (in its current context) is
+// seen, and reused afterwards.
 int rows_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return static_fail(OLB_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return static_fail(OLB_ERR_UNSUPPORTED, "device ordinal out of range");
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_rows_addr[dev]) {
+  if (!g_ctx_current) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return static_fail(OLB_ERR_CUDA, "cuCtxGetCurrent is not available from the driver");
+    }
+    g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+  }
+  // null until the runtime has made the device's primary context current; the
+  // symbol lookup below does that
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  RowsAddress& r = g_rows[dev];
+  if (!ctx || r.ctx != ctx || !r.addr) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_partial_rows);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return static_fail(OLB_ERR_CUDA, e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address");
     }
-    g_rows_addr[dev] = static_cast<double*>(p);
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return static_fail(OLB_ERR_CUDA, "no current CUDA context");
+    r.ctx = ctx;
+    r.addr = static_cast<double*>(p);
   }
-  *out = g_rows_addr[dev];
+  *out = r.addr;
   return OLB_OK;
 }
 
@@ -140,7 +162,7 @@ int olb_statistics_noalloc(olb_descriptor d, int nx, int ny, int nz, const doubl
                        "(65,536 blocks of partial sums in its fixed scratch array)");
   if (!f || !out) return static_fail(OLB_ERR_ARG, "null populations or output");
   if (!on_device(f) || !on_device(out) || (material && !on_device(material)))
-    return static_fail(OLB_ERR_ARG, "populations, material and output must be device memory");
+    return static_fail(OLB_ERR_ARG, "populations, material and output must be device memory of the current device");
   double* rows = nullptr;
   int rc = rows_address(&rows);
   if (rc) return rc;

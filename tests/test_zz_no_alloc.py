@@ -3,11 +3,14 @@ allocate device memory (their GPU memory is held by another allocator, or they
 cannot accept cudaMalloc's device-wide synchronisation).  It keeps its partial
 sums in a fixed array inside the library instead of allocating.
 
-Checked through the C ABI against the existing entry point olb_diagnostics on
-the same lattice state, on two calls in a row (the second on a later state, so
-a stale partial sum left by the first call would show), within the FP64
-tolerances of the other statistics tests.  This file is collected last so that
-a run stopping at its first failure has already run every other test.
+Checked through the C ABI against the existing entry point olb_diagnostics and
+against the oracle's statistics of the same population array, on two calls in
+a row (the second on a later state, so a stale partial sum left by the first
+call would show), within the FP64 tolerances of the other statistics tests; once
+with a material array and a force, once on an all-fluid periodic lattice with
+neither (NULL material: every cell fluid; NULL force: F = 0).  This file is
+collected last so that a run stopping at its first failure has already run every
+other test.
 """
 import ctypes
 
@@ -35,9 +38,10 @@ def _noalloc(olb, lat, f, material, force, stream):
     import torch
 
     out = torch.full((7,), float("nan"), dtype=torch.float64, device="cuda")
-    F = (ctypes.c_double * 3)(*force)
+    F = None if force is None else (ctypes.c_double * 3)(*force)
+    mat = None if material is None else material.data_ptr()
     rc = olb.load().olb_statistics_noalloc(lat.descriptor, lat.nx, lat.ny, lat.nz, f.data_ptr(),
-                                           material.data_ptr(), F, out.data_ptr(),
+                                           mat, F, out.data_ptr(),
                                            ctypes.c_void_p(stream.cuda_stream))
     assert rc == 0, olb.load().olb_last_error().decode()
     stream.synchronize()
@@ -52,26 +56,49 @@ def _agree(a, b):
     assert a[6] == b[6] == 0
 
 
-@pytest.mark.parametrize("d,shape", [(1, (30, 22, 17)), (0, (45, 33, 1))])
-def test_noalloc_statistics_match_diagnostics_twice(olb, d, shape):
+def _oracle_stats(oracle, d, m, periodic, force, f):
+    o = oracle.Lattice(d, m, 0.6, periodic=periodic, force=force or (0.0, 0.0, 0.0))
+    q = 19 if d == 1 else 9
+    return o.diagnostics(np.ascontiguousarray(f.cpu().numpy().reshape((q,) + m.shape)))
+
+
+@pytest.mark.parametrize("d,shape,walls", [(1, (30, 22, 17), True), (0, (45, 33, 1), True),
+                                           (1, (24, 18, 14), False), (0, (40, 28, 1), False)])
+def test_noalloc_statistics_match_diagnostics_twice(olb, oracle, d, shape, walls):
+    """walls=True: a cavity with a moving lid, a material array and a force.
+    walls=False: an all-fluid periodic vortex with NULL material and NULL force."""
     import torch
 
     nx, ny, nz = shape
-    m = I.cavity_box(nx, ny, nz)
-    force = (2e-6, -1e-6, 0.0)
     lat = olb.Lattice(d, shape, dtype="f64", scheme="pull")
-    lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 0)
-    lat.set_wall_velocity(I.LID, (0.05, 0.0, 0.0))
-    lat.set_bgk(0.6)
-    lat.set_force(force)
-    lat.init_equilibrium()
-    mat = torch.from_numpy(m.reshape(-1).copy()).cuda()
+    if walls:
+        m = I.cavity_box(nx, ny, nz)
+        periodic = 0
+        force = (2e-6, -1e-6, 0.0)
+        lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), periodic)
+        lat.set_wall_velocity(I.LID, (0.05, 0.0, 0.0))
+        lat.set_force(force)
+        lat.set_bgk(0.6)
+        lat.init_equilibrium()
+        mat = torch.from_numpy(m.reshape(-1).copy()).cuda()
+    else:
+        m = I.periodic_box(nx, ny, nz)
+        periodic = 7 if d == 1 else 3
+        force = None
+        lat.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), periodic)
+        lat.set_bgk(0.6)
+        rho, u = I.tgv3d(nx, 0.02) if d == 1 else I.tgv2d(nx, 0.02)
+        rho, u = rho[:nz, :ny, :nx], u[:, :nz, :ny, :nx]
+        lat.init_equilibrium(torch.from_numpy(np.ascontiguousarray(rho).reshape(-1)).cuda(),
+                             torch.from_numpy(np.ascontiguousarray(u).reshape(-1)).cuda())
+        mat = None
     stream = torch.cuda.current_stream()
     for steps in (25, 40):  # two calls in a row, on different states
         lat.step(steps)
         f = lat.get_populations()
         got = _noalloc(olb, lat, f, mat, force, stream)
         _agree(got, lat.diagnostics())
+        _agree(got, _oracle_stats(oracle, d, m, periodic, force, f))
     lat.close()
 
 
