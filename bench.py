@@ -520,6 +520,43 @@ def experiment_domain_id(torch, olb, dtype="f32", iterations=20):
     return out
 
 
+PROFILE_CASES = ("cavity128_{f32,f16,bf16}_{pull,aa}[_trt], tgv256_{f32,f16}_pull, "
+                 "adjoint_channel128_f32")
+
+
+def run_profile_case(torch, olb, case: str, launches: int):
+    """A short run of one kernel configuration for an ncu capture: set-up, then
+    `launches` step launches (or one adjoint run of `launches` steps).  Prints one
+    line; times nothing."""
+    parts = case.split("_")
+    if parts[0] == "cavity128":
+        dtype, scheme = parts[1], parts[2]
+        lat, m, noise = make_cavity(olb, torch, dtype, scheme)
+        if parts[-1] == "trt":
+            lat.set_trt(TAU, 3.0 / 16.0)
+        lat.init_equilibrium()
+        lat.perturb(noise)
+        lat.step(launches)
+    elif parts[0] == "tgv256":
+        n = 256
+        lat = olb.Lattice(olb.D3Q19, (n, n, n), dtype=parts[1], scheme=parts[2])
+        lat.set_material(torch.ones(n ** 3, dtype=torch.uint8, device="cuda"), 7)
+        lat.set_bgk(0.6)
+        rho, u = I.tgv3d(n, 0.02, xp=torch, device="cuda")
+        lat.init_equilibrium(rho.reshape(-1), u.reshape(-1))
+        del rho, u
+        lat.step(launches)
+    elif case == "adjoint_channel128_f32":
+        lat, m = porous_channel(olb, torch, 128, 64, 64, "f32")
+        lat.adjoint_run(launches, 10, (0, 127, 0))
+    else:
+        raise SystemExit(f"unknown profile case {case!r}; cases: {PROFILE_CASES}")
+    torch.cuda.synchronize()
+    t, k = lat.counters()
+    lat.close()
+    print(json.dumps({"profile_case": case, "lbm_steps": t, "kernel_launches": k}), flush=True)
+
+
 def reduce_over_ranks(torch, world: int, maxes, sums, device):
     """Whole-job figures of a multi-rank run: the max over ranks of each value in
     `maxes` (times) and the sum over ranks of each value in `sums` (counts), through
@@ -693,7 +730,18 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--experiment", choices=["adjoint384", "domain_id", "fd256"], default=None,
                     help="run a named experiment instead of the benchmark and print its JSON")
+    ap.add_argument("--profile", default=None, metavar="CASE",
+                    help="run one kernel configuration briefly for an ncu capture: " + PROFILE_CASES)
+    ap.add_argument("--launches", type=int, default=6, help="step launches of --profile")
     args = ap.parse_args()
+    if args.profile is not None:
+        import torch
+
+        from paper_2307_11752_gb300 import build, olb
+        build.build()
+        olb.load()
+        run_profile_case(torch, olb, args.profile, args.launches)
+        return
     if args.experiment is not None:
         import torch
 
