@@ -395,23 +395,35 @@ def experiment_adjoint384(torch, olb, fd_cells=4):
     return res
 
 
-def experiment_fd256(torch, olb, cells=64):
-    """The differentiable channel at its full size: 256x128x128, FP32 storage, 2000
-    steps, checkpoints every 100, loss = mean u_x on the outlet plane x = 255.  The
-    adjoint's dL/dgamma at `cells` seeded random fluid cells and dL/dtau against
-    central differences of FP64 forward runs on the GPU (h = 1e-5 for gamma, 1e-6 for
-    tau)."""
+def experiment_fd256(torch, olb, cells=64, h=1e-3, richardson_cells=8):
+    """The differentiable channel at its full size: 256x128x128, 2000 steps,
+    checkpoints every 100, loss = mean u_x on the outlet plane x = 255.  The FP32- and
+    FP64-storage adjoints' dL/dgamma at `cells` seeded random fluid cells and dL/dtau
+    against central differences of FP64 forward runs on the GPU, and the FP32 adjoint
+    against the FP64 adjoint at every fluid cell.
+
+    Step of the differences: the loss is ~4e-6 and dL/dgamma ~1e-13 .. 1e-11 per cell,
+    so at h = 1e-5 the two losses of a quotient differ only in their last ~5
+    significant digits and the quotient carries FP64 rounding noise of 1e-5 .. 1e-3
+    relative.  h = 1e-3 (gamma stays inside [0, 1]) moves the loss 100 times more; the
+    truncation error of the central quotient is checked at `richardson_cells` cells by
+    repeating them with h/2 (the two quotients differ by 3/4 of the h^2 error term)."""
     nx, ny, nz, steps, K = 256, 128, 128, 2000, 100
     obj = (0, nx - 1, 0)
-    lat, m = porous_channel(olb, torch, nx, ny, nz, "f32")
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    loss, dg, dtau = lat.adjoint_run(steps, K, obj)
-    torch.cuda.synchronize()
-    adj_sec = time.perf_counter() - t
-    dg = dg.cpu().numpy().reshape(-1)
-    lat.close()
-    torch.cuda.empty_cache()
+    grads = {}
+    secs = {}
+    for dtype in ("f32", "f64"):
+        lat, m = porous_channel(olb, torch, nx, ny, nz, dtype)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        loss, dg, dtau = lat.adjoint_run(steps, K, obj)
+        torch.cuda.synchronize()
+        secs[dtype] = round(time.perf_counter() - t, 2)
+        grads[dtype] = (loss, dg.cpu().numpy().reshape(-1), dtau)
+        lat.close()
+        del dg
+        torch.cuda.empty_cache()
+    g32, g64 = grads["f32"][1], grads["f64"][1]
     gamma = I.smoothed_porosity(2, m)
     ref = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype="f64", scheme="pull")
     ref.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 1)
@@ -426,25 +438,41 @@ def experiment_fd256(torch, olb, cells=64):
         _, u = ref.moments()
         return float(u[0, :, :, nx - 1][plane].mean())
 
-    t = time.perf_counter()
-    rel = []
-    for c in I.random_fluid_cells(3, m, cells):
+    def quotient(c, hh):
         gp = gamma.reshape(-1).copy()
         gm = gp.copy()
-        gp[c] += 1e-5
-        gm[c] -= 1e-5
-        d = (run(gp, 0.8) - run(gm, 0.8)) / 2e-5
-        rel.append(abs(dg[c] - d) / abs(d))
-    d = (run(gamma, 0.8 + 1e-6) - run(gamma, 0.8 - 1e-6)) / 2e-6
+        gp[c] += hh
+        gm[c] -= hh
+        return (run(gp, 0.8) - run(gm, 0.8)) / (2 * hh)
+
+    t = time.perf_counter()
+    sel = I.random_fluid_cells(3, m, cells)
+    fd = np.array([quotient(c, h) for c in sel])
+    rich = [abs(quotient(c, h / 2) - d) / abs(d) for c, d in zip(sel[:richardson_cells], fd[:richardson_cells])]
+    d_tau = (run(gamma, 0.8 + 1e-6) - run(gamma, 0.8 - 1e-6)) / 2e-6
+    fd_sec = time.perf_counter() - t
     ref.close()
-    rel = np.array(rel)
+    r32 = np.abs(g32[sel] - fd) / np.abs(fd)
+    r64 = np.abs(g64[sel] - fd) / np.abs(fd)
+    fl = (m == I.FLUID).reshape(-1)
+    rall = np.abs(g32[fl] - g64[fl]) / np.abs(g64[fl])
     return {
-        "workload": f"porous channel {nx}x{ny}x{nz}, FP32 storage, {steps} steps, K={K}, loss = mean u_x on x = {nx - 1}",
-        "adjoint_seconds": round(adj_sec, 2), "loss": loss, "dL_dtau": dtau,
-        "fd_cells": int(len(rel)), "fd_seconds": round(time.perf_counter() - t, 1),
-        "dgamma_rel_err_max": float(rel.max()), "dgamma_rel_err_median": float(np.median(rel)),
-        "dgamma_cells_within_1e-4": int((rel <= 1e-4).sum()),
-        "dtau_fd": d, "dtau_rel_err": abs(dtau - d) / abs(d),
+        "workload": f"porous channel {nx}x{ny}x{nz}, {steps} steps, K={K}, loss = mean u_x on x = {nx - 1}",
+        "adjoint_seconds": secs, "loss": grads["f32"][0], "dL_dtau": grads["f32"][2],
+        "fd": {"cells": int(len(sel)), "h_gamma": h, "h_tau": 1e-6, "seconds": round(fd_sec, 1),
+               "truncation_check_h_vs_h/2_rel_max": float(max(rich)),
+               "dgamma_abs_range": [float(np.abs(fd).min()), float(np.abs(fd).max())]},
+        "f32_vs_fd": {"rel_max": float(r32.max()), "rel_median": float(np.median(r32)),
+                      "cells_within_1e-4": int((r32 <= 1e-4).sum()),
+                      "dtau_rel": abs(grads["f32"][2] - d_tau) / abs(d_tau)},
+        "f64_vs_fd": {"rel_max": float(r64.max()), "rel_median": float(np.median(r64)),
+                      "cells_within_1e-6": int((r64 <= 1e-6).sum()),
+                      "dtau_rel": abs(grads["f64"][2] - d_tau) / abs(d_tau)},
+        "f32_vs_f64_all_fluid_cells": {"rel_median": float(np.median(rall)),
+                                       "rel_p99": float(np.quantile(rall, 0.99)),
+                                       "rel_p9999": float(np.quantile(rall, 0.9999)),
+                                       "abs_max_over_max_gradient": float(np.abs(g32[fl] - g64[fl]).max()
+                                                                          / np.abs(g64[fl]).max())},
     }
 
 

@@ -17,7 +17,7 @@
  * section "Derivative Computation", taken here as the exact discrete adjoint);
  * olb_adjoint_run_misfit does the same for the velocity misfit of the guide's
  * optimisation examples.  olb_set_trt selects the TRT collision instead of BGK
- * (forward only).  The olb_ade_* calls run a separate advection-diffusion
+ * (forward and adjoint).  The olb_ade_* calls run a separate advection-diffusion
  * lattice (D2Q5 / D3Q7, section "Advection--Diffusion Equation").
  *
  * Conventions shared by every call
@@ -80,7 +80,8 @@ typedef enum {
   OLB_ERR_OOM = -3,         /* the allocator returned no memory */
   OLB_ERR_STATE = -4,       /* call not valid in the handle's current state */
   OLB_ERR_NONFINITE = -5,   /* a NaN or Inf population was found */
-  OLB_ERR_TIMEOUT = -6,     /* reserved: no call of this version waits on the device */
+  OLB_ERR_TIMEOUT = -6,     /* a kernel's bounded wait on its own asynchronous copies ran out (reported
+                               by the next synchronising call; the state is then invalid) */
   OLB_ERR_UNSUPPORTED = -7  /* combination not implemented */
 } olb_status;
 
@@ -143,13 +144,24 @@ int olb_set_bgk(olb_handle h, double tau);
  * magic parameter Lambda = (1/omega+ - 1/2)(1/omega- - 1/2); the Guo source is
  * split the same way.  Lambda = (tau - 1/2)^2 is BGK; Lambda = 3/16 puts halfway
  * bounce-back walls exactly at the wall for Poiseuille flow at every tau.
- * olb_set_bgk switches back.  olb_adjoint_run and olb_adjoint_run_misfit return
- * OLB_ERR_UNSUPPORTED while TRT is selected (the adjoint is written for BGK).
+ * olb_set_bgk switches back.  olb_adjoint_run and olb_adjoint_run_misfit
+ * differentiate the TRT map while it is selected; their dL/dtau holds the magic
+ * parameter fixed (omega- follows tau).
  * Errors: OLB_ERR_ARG unless tau > 1/2 and magic > 0. */
 int olb_set_trt(olb_handle h, double tau, double magic);
 
 /* Uniform body force density F (Guo forcing with u = (j + F/2)/rho, Eqs. FBD, dF). */
 int olb_set_force(olb_handle h, const double F[3]);
+
+/* Per-cell force density F(x) (double [3][cells], host or device; the z row is
+ * ignored on D2Q9): the external force field that the guide's descriptors carry
+ * per cell (section "Lattice Boltzmann Methods": FORCE field; lesson on external
+ * forces) and that testFlowOpti3d identifies.  While a field is set it replaces
+ * the uniform force of olb_set_force in the collision (Guo forcing with the cell's
+ * own F), in u = (j + F/2)/rho of olb_moments, olb_diagnostics and the objectives.
+ * The values are copied (stored in the compute precision).  NULL removes the field.
+ * Lattices with a field run the one-cell-per-thread step kernel. */
+int olb_set_force_field(olb_handle h, const double* F);
 
 /* Per-cell porosity gamma in [0,1] (double [cells]); the equilibrium and the
  * forcing term use gamma*u (section "Porous Media Model").  The values are
@@ -213,7 +225,7 @@ typedef struct {
  * be NULL.  Device memory: (ceil(n/K) + K) copies of the state plus two adjoint
  * fields (K = checkpoint_every).
  * Errors: OLB_ERR_ARG (n_steps < 1, K < 1, bad objective or empty plane),
- *         OLB_ERR_UNSUPPORTED (TRT collision selected), OLB_ERR_OOM. */
+ *         OLB_ERR_OOM. */
 int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
                     const olb_objective* obj, double* loss, double* dL_dgamma,
                     double* dL_dtau);
@@ -232,14 +244,52 @@ int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
  * Outputs as olb_adjoint_run: loss = J, dL_dgamma = dJ/dgamma (double [cells],
  * device or host), dL_dtau = dJ/dtau.
  * Errors: OLB_ERR_ARG (n_steps < 1, K < 1, NULL u_target, region without fluid
- *         cells), OLB_ERR_UNSUPPORTED (TRT collision selected), OLB_ERR_OOM. */
+ *         cells), OLB_ERR_OOM. */
 int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t checkpoint_every,
                            const double* u_target, const uint8_t* region, double* loss,
                            double* dL_dgamma, double* dL_dtau);
 
+/* Outputs of olb_adjoint_gradients; any pointer may be NULL (not computed).
+ *   loss       host double: the objective
+ *   dL_dgamma  double [cells], host or device: gradient with respect to the porosity
+ *   dL_dtau    host double: gradient with respect to tau (TRT: magic parameter fixed)
+ *   dL_dF      double [3][cells], host or device: gradient with respect to the force
+ *              density of every cell (zero on non-fluid cells and, on D2Q9, in the z
+ *              row), whether the force is a field or uniform: the control of the
+ *              guide's force-field identification (testFlowOpti3d).  It collects the
+ *              force's three routes: u = (j + F/2)/rho in the collision, the Guo
+ *              source itself, and u in the objective. */
+typedef struct {
+  double* loss;
+  double* dL_dgamma;
+  double* dL_dtau;
+  double* dL_dF;
+} olb_gradients;
+
+/* The checkpointed adjoint run of olb_adjoint_run (obj != NULL, u_target == NULL)
+ * or of olb_adjoint_run_misfit (obj == NULL, u_target and region as there), with
+ * every gradient output of olb_gradients.  dL_dF costs 3 double fields more device
+ * memory and one read-modify-write of them per adjoint step.
+ * Errors: as those calls; OLB_ERR_ARG also for out == NULL, or for both or neither
+ *         of obj and u_target. */
+int olb_adjoint_gradients(olb_handle h, int64_t n_steps, int64_t checkpoint_every, const olb_objective* obj,
+                          const double* u_target, const uint8_t* region, olb_gradients* out);
+
 /* Block the host until all work queued on the handle's stream has finished;
  * reports asynchronous CUDA errors as OLB_ERR_CUDA. */
 int olb_synchronize(olb_handle h);
+
+/* Failure injection for tests of the device-side timeout path (not for production
+ * use; the guide has no counterpart).  The next step of the handle that runs the
+ * TMA-fed pull kernel (FP32 or 16-bit storage, even nx, no force field; the state
+ * after a pull step) expects `extra_bytes` more than its tile copies deliver, so
+ * that the bounded wait of every block runs out after `wait_ns` nanoseconds.  The
+ * blocks then record the failure, let their copies land and return: the step's
+ * output is invalid, and the next synchronising call (olb_synchronize,
+ * olb_step_stats, olb_diagnostics) returns OLB_ERR_TIMEOUT and clears it.  The
+ * context stays usable.  Applies to one step; extra_bytes = 0 clears it.
+ * Errors: OLB_ERR_ARG (extra_bytes > 65536, wait_ns outside [1e6, 5e9]). */
+int olb_inject_stalled_copy(olb_handle h, unsigned extra_bytes, int64_t wait_ns);
 
 /* Time step counter (steps since the last olb_init_equilibrium /
  * olb_set_populations) and the number of kernels the handle has launched. */

@@ -1,11 +1,14 @@
 // olb_api.cu -- the C ABI of include/olb.h: handle state, argument checks,
 // host/device staging, representation bookkeeping and the checkpointed adjoint.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -235,6 +238,56 @@ void link_masks(int nx, int ny, int nz, unsigned periodic, const uint8_t* mat, u
 
 }  // namespace
 
+int olb::tma_setting(const char* name, int fallback) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::string, int>> seen;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& kv : seen)
+    if (kv.first == name) return kv.second;
+  int v = fallback;
+  if (const char* s = std::getenv(name)) {
+    char* end = nullptr;
+    const long x = std::strtol(s, &end, 10);
+    if (end != s && *end == '\0') v = (int)x;
+  }
+  seen.emplace_back(name, v);
+  return v;
+}
+
+int olb::device_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+bool olb::encode_population_map(void* map, int elem_bytes, bool bf16, const void* base, int nx, int ny, int nz,
+                                int q, int pitch, int box_x, int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult r;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &r) == cudaSuccess &&
+        r == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cudaGetLastError();
+  });
+  if (!encode) return false;
+  const CUtensorMapDataType type = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)q};
+  const cuuint64_t strides[3] = {(cuuint64_t)nx * elem_bytes, (cuuint64_t)nx * ny * elem_bytes,
+                                 (cuuint64_t)pitch * elem_bytes};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_rows, 1, 1};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return encode(static_cast<CUtensorMap*>(map), type, 4, const_cast<void*>(base), dims, strides, box, estride,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 MemKind olb::mem_kind(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -265,7 +318,7 @@ struct olb_lattice {
   cudaStream_t stream = nullptr;
   DevBuf buf[2];
   int cur = 0, repr = PRE, scheme = OLB_PULL;
-  DevBuf mat, cls, wmask, pmask, word, wall_u, gamma, partials, out8;
+  DevBuf mat, cls, wmask, pmask, word, wall_u, gamma, ffield, partials, out8, err;
   bool outside_links = false;
   int y0 = 0, y1 = 0, z0 = 0, z1 = 0;  // bounding rows of the fluid cells
   std::vector<uint8_t> h_mat;
@@ -277,6 +330,9 @@ struct olb_lattice {
   bool trt = false;     // collision operator: BGK, or TRT with magic parameter `magic`
   double magic = 0.25;
   bool has_gamma = false;
+  bool has_ffield = false;  // a per-cell force density replaces the uniform force
+  unsigned inject_tx = 0;   // failure injection for the next step (olb_inject_stalled_copy)
+  int64_t inject_ns = 0;
   int64_t time = 0, launches = 0;
 
   size_t state_bytes() const { return (size_t)q * pitch * kt->state_elem; }
@@ -299,9 +355,13 @@ struct olb_lattice {
     p.omega = 1.0 / tau;
     p.trt = trt ? 1 : 0;
     p.omega_minus = trt ? 1.0 / (magic / (tau - 0.5) + 0.5) : p.omega;
+    // omega- = 1/(Lambda/a + 1/2) with a = 1/omega - 1/2: d omega-/d omega = -omega-^2 Lambda/(a omega)^2
+    p.domega_minus = trt ? -p.omega_minus * p.omega_minus * magic / ((tau - 0.5) * (tau - 0.5) * p.omega * p.omega)
+                         : 1.0;
     for (int a = 0; a < 3; ++a) p.force[a] = F[a];
     p.forced = (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0) ? 1 : 0;
     p.gamma = has_gamma ? gamma.p : nullptr;
+    p.ffield = has_ffield ? ffield.p : nullptr;
     p.pmask = static_cast<const uint32_t*>(pmask.p);
     p.word = static_cast<const uint32_t*>(word.p);
     p.outside_links = outside_links ? 1 : 0;
@@ -309,11 +369,19 @@ struct olb_lattice {
     p.y1 = y1;
     p.z0 = z0;
     p.z1 = z1;
+    p.err = static_cast<unsigned*>(err.p);
+    p.inject_extra_tx = inject_tx;
+    p.inject_wait_ns = (unsigned long long)inject_ns;
     p.stream = stream;
     return p;
   }
   // blocks (= rows of partial sums) of the step kernel and of the per-cell kernels
-  int64_t step_rows() const { return make_step_grid(params(), dtype != OLB_F64 && pairs_ok(nx)).blocks(); }
+  // rows of partial sums the step kernels may write (the largest of their grids)
+  int64_t step_rows() const {
+    const HostParams p = params();
+    int64_t r = make_step_grid(p, dtype != OLB_F64 && pairs_ok(nx) && !has_ffield).blocks();
+    return std::max(r, kt->step_rows(p, G_PULL, S_OWN));
+  }
   int64_t cell_rows() const { return make_grid(nx, ny, nz).blocks(); }
   int64_t grid_blocks() const { return std::max(step_rows(), cell_rows()); }
 };
@@ -453,47 +521,73 @@ int materialize(olb_handle h) {
   return OLB_OK;
 }
 
-// One collide-and-stream step in the handle's scheme.
-int step_once(olb_handle h, bool stats, double* partials) {
+// One collide-and-stream step in the handle's scheme.  `rows`, when given,
+// receives the number of partial-sum rows the step kernel wrote (stats).
+int step_once(olb_handle h, bool stats, double* partials, int64_t* rows = nullptr) {
   HostParams p = h->params();
   const KernelTable* kt = h->kt;
   int rc;
   void* a = h->buf[h->cur].p;
+  int g, sc;
   if (h->scheme == OLB_PULL) {
+    sc = S_OWN;
     if (h->repr == PRE) {
-      rc = launched(h, kt->step(p, G_OWN, S_OWN, stats, a, a, partials), "step");
+      g = G_OWN;
+      rc = launched(h, kt->step(p, g, sc, stats, a, a, partials), "step");
     } else {
       if ((rc = ensure_other(h))) return rc;
       void* b = h->buf[1 - h->cur].p;
-      rc = launched(h, kt->step(p, gather_of(h->repr), S_OWN, stats, a, b, partials), "step");
+      g = gather_of(h->repr);
+      rc = launched(h, kt->step(p, g, sc, stats, a, b, partials), "step");
       if (!rc) h->cur = 1 - h->cur;
     }
     if (rc) return rc;
     h->repr = POST;
   } else {
     if (h->repr == PRE) {
-      rc = launched(h, kt->step(p, G_OWN, S_OWN_SWAP, stats, a, a, partials), "step");
+      g = G_OWN;
+      sc = S_OWN_SWAP;
+      rc = launched(h, kt->step(p, g, sc, stats, a, a, partials), "step");
       if (rc) return rc;
       h->repr = AA_ODD;
     } else if (h->repr == AA_ODD) {
-      rc = launched(h, kt->step(p, G_PULL_SWAP, S_PUSH, stats, a, a, partials), "step");
+      g = G_PULL_SWAP;
+      sc = S_PUSH;
+      rc = launched(h, kt->step(p, g, sc, stats, a, a, partials), "step");
       if (rc) return rc;
       h->repr = PRE;
     } else {
       if ((rc = ensure_other(h))) return rc;
       void* b = h->buf[1 - h->cur].p;
-      rc = launched(h, kt->step(p, G_PULL, S_OWN_SWAP, stats, a, b, partials), "step");
+      g = G_PULL;
+      sc = S_OWN_SWAP;
+      rc = launched(h, kt->step(p, g, sc, stats, a, b, partials), "step");
       if (rc) return rc;
       h->cur = 1 - h->cur;
       h->repr = AA_ODD;
     }
   }
+  if (rows) *rows = kt->step_rows(p, g, sc);
+  h->inject_tx = 0;  // an injection applies to one step
   h->time++;
+  return OLB_OK;
+}
+
+// Reads and clears the handle's error word (synchronises the stream).
+int check_error_word(olb_handle h) {
+  unsigned v = 0;
+  OLB_CUDA(cudaMemcpyAsync(&v, h->err.p, sizeof(v), cudaMemcpyDeviceToHost, h->stream), "error word read");
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "error word sync");
+  if (v) {
+    OLB_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof(unsigned), h->stream), "error word clear");
+    return fail(OLB_ERR_TIMEOUT, "a step kernel gave up waiting for its tile copies; the state is invalid");
+  }
   return OLB_OK;
 }
 
 // Convert the 8 reduced statistics to the ABI's 7 and deliver them.
 int deliver_stats(olb_handle h, double* out) {
+  if (int rc = check_error_word(h)) return rc;
   double r[8];
   OLB_CUDA(cudaMemcpyAsync(r, h->out8.p, sizeof(r), cudaMemcpyDeviceToHost, h->stream), "stats copy");
   OLB_CUDA(cudaStreamSynchronize(h->stream), "stats sync");
@@ -546,7 +640,7 @@ int upload_wall(olb_handle h) {
 // loss = loss_scale * (sum of row 0).
 template <class Seed>
 int adjoint_sweep(olb_handle h, int64_t n_steps, int64_t K, Seed&& seed, double loss_scale, double* loss,
-                  double* dL_dgamma, double* dL_dtau) {
+                  double* dL_dgamma, double* dL_dtau, double* dL_dF = nullptr) {
   int rc;
   if (K > n_steps) K = n_steps;
   const int64_t nseg = (n_steps + K - 1) / K;
@@ -557,7 +651,7 @@ int adjoint_sweep(olb_handle h, int64_t n_steps, int64_t K, Seed&& seed, double 
   // buffers: checkpoints, segment slots 1..K-1, two adjoint fields, gradients
   std::vector<DevBuf> ckpt(nseg), seg(K);
   std::vector<int> ckpt_repr(nseg);
-  DevBuf lam[2], dg, part;
+  DevBuf lam[2], dg, dF, part;
   for (auto& b : ckpt)
     if ((rc = b.reserve(sb))) return rc;
   for (int64_t k = 1; k < K; ++k)
@@ -565,6 +659,8 @@ int adjoint_sweep(olb_handle h, int64_t n_steps, int64_t K, Seed&& seed, double 
   if ((rc = lam[0].reserve(lb)) || (rc = lam[1].reserve(lb)) || (rc = dg.reserve((size_t)h->ncell * 8)) ||
       (rc = part.reserve((size_t)rows * 8 * sizeof(double))) || (rc = ensure_partials(h, h->grid_blocks())))
     return rc;
+  if (dL_dF && (rc = dF.reserve((size_t)3 * h->ncell * sizeof(double)))) return rc;
+  double* dFp = dL_dF ? static_cast<double*>(dF.p) : nullptr;
   if (h->repr == AA_ODD && (rc = materialize(h))) return rc;
 
   // forward sweep with checkpoints (pull pattern)
@@ -586,7 +682,7 @@ int adjoint_sweep(olb_handle h, int64_t n_steps, int64_t K, Seed&& seed, double 
   HostParams p = h->params();
   const KernelTable* kt = h->kt;
   double* partials = static_cast<double*>(h->partials.p);
-  if ((rc = launched(h, seed(p, h->buf[h->cur].p, lam[0].p, partials), "loss"))) return rc;
+  if ((rc = launched(h, seed(p, h->buf[h->cur].p, lam[0].p, dFp, partials), "loss"))) return rc;
   if ((rc = launched(h, reduce_partials(partials, rows, static_cast<double*>(h->out8.p), h->stream), "loss reduce")))
     return rc;
   double lsum[8];
@@ -611,7 +707,7 @@ int adjoint_sweep(olb_handle h, int64_t n_steps, int64_t K, Seed&& seed, double 
     for (int64_t k = ks - 1; k >= 0; --k) {
       const int g = srepr[k] == PRE ? G_OWN : G_PULL;
       if ((rc = launched(h, kt->adjoint(p, g, slot[k], lam[li].p, lam[1 - li].p, static_cast<double*>(dg.p),
-                                        static_cast<double*>(part.p)), "adjoint")))
+                                        dFp, static_cast<double*>(part.p)), "adjoint")))
         return rc;
       li = 1 - li;
     }
@@ -622,6 +718,10 @@ int adjoint_sweep(olb_handle h, int64_t n_steps, int64_t K, Seed&& seed, double 
   OLB_CUDA(cudaMemcpyAsync(gsum, h->out8.p, sizeof(gsum), cudaMemcpyDeviceToHost, h->stream), "gradient copy");
   if (dL_dgamma) {
     OLB_CUDA(cudaMemcpyAsync(dL_dgamma, dg.p, (size_t)h->ncell * 8, cudaMemcpyDefault, h->stream), "gradient out");
+  }
+  if (dL_dF) {
+    OLB_CUDA(cudaMemcpyAsync(dL_dF, dF.p, (size_t)3 * h->ncell * 8, cudaMemcpyDefault, h->stream),
+             "force gradient out");
   }
   OLB_CUDA(cudaStreamSynchronize(h->stream), "adjoint sync");
   if (loss) *loss = lsum[0] * loss_scale;
@@ -642,7 +742,7 @@ const char* olb_last_error(void) { return g_err.c_str(); }
 #define OLB_STR(x) OLB_STR2(x)
 const char* olb_build_info(void) {
   return "sm_103a step_min_blocks=" OLB_STR(OLB_STEP_MIN_BLOCKS) " pair_min_blocks=" OLB_STR(OLB_PAIR_MIN_BLOCKS) " pair16_min_blocks=" OLB_STR(OLB_PAIR16_MIN_BLOCKS) " pair16_walls_min_blocks=" OLB_STR(OLB_PAIR16_WALLS_MIN_BLOCKS) " ghost16=" OLB_STR(OLB_GHOST_FIRST16) OLB_STR(OLB_GHOST_COORDS16) " ghost32=" OLB_STR(OLB_GHOST_FIRST32) OLB_STR(OLB_GHOST_COORDS32)
-         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " xwall_pairs=" OLB_STR(OLB_XWALL_PAIRS) " fluid_box=" OLB_STR(OLB_FLUID_BOX) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
+         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " xwall_pairs=" OLB_STR(OLB_XWALL_PAIRS) " fluid_box=" OLB_STR(OLB_FLUID_BOX) " pdl=" OLB_STR(OLB_PDL) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
 #ifdef OLB_NO_PAIRS
          " pairs=off"
 #else
@@ -693,13 +793,18 @@ int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, ol
   int rc;
   if ((rc = h->buf[0].reserve(h->state_bytes())) || (rc = h->mat.reserve(cells)) ||
       (rc = h->cls.reserve(cells)) || (rc = h->wmask.reserve(cells * 4)) || (rc = h->pmask.reserve(cells * 4)) ||
-      (rc = h->word.reserve(cells * 4)) ||
+      (rc = h->word.reserve(cells * 4)) || (rc = h->err.reserve(sizeof(unsigned))) ||
       (rc = h->wall_u.reserve(sizeof(h->h_wall) + sizeof(h->h_wall_f))) ||
       (rc = ensure_partials(h, h->grid_blocks()))) {
     std::string msg = g_err;
     delete h;
     g_err = msg;
     return rc;
+  }
+  if (cudaMemset(h->err.p, 0, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(OLB_ERR_CUDA, "error word clear failed");
   }
   // all fluid, nothing periodic: every boundary link bounces back
   h->h_mat.assign(cells, OLB_MAT_FLUID);
@@ -860,6 +965,12 @@ __global__ void k_convert_gamma(const double* __restrict__ in, C* __restrict__ o
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (C)in[i];
 }
+// out[i] = in[i] for i < zero_from, 0 for zero_from <= i < n.
+template <class C>
+__global__ void k_convert_field(const double* __restrict__ in, C* __restrict__ out, int64_t n, int64_t zero_from) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = i < zero_from ? (C)in[i] : C(0);
+}
 }  // namespace olb
 
 extern "C" {
@@ -883,6 +994,32 @@ int olb_set_porosity(olb_handle h, const double* gamma) {
   if ((rc = launched(h, cudaGetLastError(), "porosity"))) return rc;
   if (tmp.p) OLB_CUDA(cudaStreamSynchronize(h->stream), "porosity sync");
   h->has_gamma = true;
+  return OLB_OK;
+}
+
+int olb_set_force_field(olb_handle h, const double* F) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!F) {
+    h->has_ffield = false;
+    return OLB_OK;
+  }
+  DevBuf tmp;
+  const void* src;
+  if ((rc = input_view(h, F, (size_t)3 * h->ncell * sizeof(double), tmp, &src))) return rc;
+  if ((rc = h->ffield.reserve((size_t)3 * h->ncell * h->compute_elem()))) return rc;
+  const int64_t n = (int64_t)3 * h->ncell;
+  const int nb = (int)((n + 255) / 256);
+  const int64_t zero_from = h->dim == 2 ? (int64_t)2 * h->ncell : n;  // D2Q9: no z component
+  if (h->dtype == OLB_F64)
+    k_convert_field<double><<<nb, 256, 0, h->stream>>>(static_cast<const double*>(src),
+                                                       static_cast<double*>(h->ffield.p), n, zero_from);
+  else
+    k_convert_field<float><<<nb, 256, 0, h->stream>>>(static_cast<const double*>(src),
+                                                      static_cast<float*>(h->ffield.p), n, zero_from);
+  if ((rc = launched(h, cudaGetLastError(), "force field"))) return rc;
+  if (tmp.p) OLB_CUDA(cudaStreamSynchronize(h->stream), "force field sync");
+  h->has_ffield = true;
   return OLB_OK;
 }
 
@@ -965,11 +1102,11 @@ int olb_step_stats(olb_handle h, int64_t n, double* out) {
   if (rc) return rc;
   if (n < 1) return fail(OLB_ERR_ARG, "olb_step_stats needs n >= 1");
   if (!out) return fail(OLB_ERR_ARG, "null output");
-  const int64_t rows = h->step_rows();
-  if ((rc = ensure_partials(h, rows))) return rc;
+  if ((rc = ensure_partials(h, h->step_rows()))) return rc;
   for (int64_t s = 0; s + 1 < n; ++s)
     if ((rc = step_once(h, false, nullptr))) return rc;
-  if ((rc = step_once(h, true, static_cast<double*>(h->partials.p)))) return rc;
+  int64_t rows = 0;
+  if ((rc = step_once(h, true, static_cast<double*>(h->partials.p), &rows))) return rc;
   if ((rc = launched(h, reduce_partials(static_cast<double*>(h->partials.p), rows, static_cast<double*>(h->out8.p), h->stream), "stats reduce")))
     return rc;
   return deliver_stats(h, out);
@@ -1015,6 +1152,17 @@ int olb_synchronize(olb_handle h) {
   if (rc) return rc;
   OLB_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
   OLB_CUDA(cudaGetLastError(), "asynchronous error");
+  return check_error_word(h);
+}
+
+int olb_inject_stalled_copy(olb_handle h, unsigned extra_bytes, int64_t wait_ns) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (extra_bytes > 65536u) return fail(OLB_ERR_ARG, "extra_bytes above 65536");
+  if (extra_bytes && (wait_ns < 1000000 || wait_ns > 5000000000LL))
+    return fail(OLB_ERR_ARG, "wait_ns outside [1 ms, 5 s]");
+  h->inject_tx = extra_bytes;
+  h->inject_ns = wait_ns;
   return OLB_OK;
 }
 
@@ -1026,12 +1174,15 @@ int olb_counters(olb_handle h, int64_t* time, int64_t* kernel_launches) {
   return OLB_OK;
 }
 
-int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t K, const olb_objective* obj,
-                    double* loss, double* dL_dgamma, double* dL_dtau) {
-  int rc = check(h);
-  if (rc) return rc;
+}  // extern "C"
+
+namespace {
+
+// The checkpointed adjoint of the plane-mean objective (obj) or of the velocity
+// misfit (u_target, region), with every gradient output (any may be null).
+int adjoint_plane(olb_handle h, int64_t n_steps, int64_t K, const olb_objective* obj, double* loss,
+                  double* dL_dgamma, double* dL_dtau, double* dL_dF) {
   if (n_steps < 1 || K < 1) return fail(OLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
-  if (h->trt) return fail(OLB_ERR_UNSUPPORTED, "the adjoint is written for the BGK collision");
   if (!obj || obj->plane_axis < 0 || obj->plane_axis >= h->dim || obj->component < 0 || obj->component >= h->dim)
     return fail(OLB_ERR_ARG, "bad objective");
   const int ext[3] = {h->nx, h->ny, h->nz};
@@ -1047,19 +1198,17 @@ int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t K, const olb_objectiv
       }
   if (count == 0) return fail(OLB_ERR_ARG, "objective plane holds no fluid cell");
   const double inv_count = 1.0 / (double)count;
-  auto seed = [&](const HostParams& p, const void* state, void* lam0, double* partials) {
+  auto seed = [&](const HostParams& p, const void* state, void* lam0, double* dforce, double* partials) {
     return h->kt->loss_seed(p, gather_of(h->repr), state, obj->plane_axis, obj->plane_index, obj->component,
-                            inv_count, lam0, partials);
+                            inv_count, lam0, dforce, partials);
   };
-  return adjoint_sweep(h, n_steps, K, seed, inv_count, loss, dL_dgamma, dL_dtau);
+  return adjoint_sweep(h, n_steps, K, seed, inv_count, loss, dL_dgamma, dL_dtau, dL_dF);
 }
 
-int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t K, const double* u_target,
-                           const uint8_t* region, double* loss, double* dL_dgamma, double* dL_dtau) {
-  int rc = check(h);
-  if (rc) return rc;
+int adjoint_misfit(olb_handle h, int64_t n_steps, int64_t K, const double* u_target, const uint8_t* region,
+                   double* loss, double* dL_dgamma, double* dL_dtau, double* dL_dF) {
+  int rc;
   if (n_steps < 1 || K < 1) return fail(OLB_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
-  if (h->trt) return fail(OLB_ERR_UNSUPPORTED, "the adjoint is written for the BGK collision");
   if (!u_target) return fail(OLB_ERR_ARG, "null target velocity");
   const size_t n = (size_t)h->ncell;
   // the region on the host, to count its fluid cells before any work is queued
@@ -1078,11 +1227,40 @@ int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t K, const doubl
   const void* rg = nullptr;
   if ((rc = input_view(h, u_target, 3 * n * sizeof(double), ut_tmp, &ut))) return rc;
   if (region && (rc = input_view(h, region, n, reg_tmp, &rg))) return rc;
-  auto seed = [&](const HostParams& p, const void* state, void* lam0, double* partials) {
+  auto seed = [&](const HostParams& p, const void* state, void* lam0, double* dforce, double* partials) {
     return h->kt->misfit_seed(p, gather_of(h->repr), state, static_cast<const double*>(ut),
-                              static_cast<const uint8_t*>(rg), lam0, partials);
+                              static_cast<const uint8_t*>(rg), lam0, dforce, partials);
   };
-  return adjoint_sweep(h, n_steps, K, seed, 1.0, loss, dL_dgamma, dL_dtau);
+  return adjoint_sweep(h, n_steps, K, seed, 1.0, loss, dL_dgamma, dL_dtau, dL_dF);
+}
+
+}  // namespace
+
+extern "C" {
+
+int olb_adjoint_run(olb_handle h, int64_t n_steps, int64_t K, const olb_objective* obj,
+                    double* loss, double* dL_dgamma, double* dL_dtau) {
+  int rc = check(h);
+  if (rc) return rc;
+  return adjoint_plane(h, n_steps, K, obj, loss, dL_dgamma, dL_dtau, nullptr);
+}
+
+int olb_adjoint_run_misfit(olb_handle h, int64_t n_steps, int64_t K, const double* u_target,
+                           const uint8_t* region, double* loss, double* dL_dgamma, double* dL_dtau) {
+  int rc = check(h);
+  if (rc) return rc;
+  return adjoint_misfit(h, n_steps, K, u_target, region, loss, dL_dgamma, dL_dtau, nullptr);
+}
+
+int olb_adjoint_gradients(olb_handle h, int64_t n_steps, int64_t K, const olb_objective* obj,
+                          const double* u_target, const uint8_t* region, olb_gradients* out) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (!out) return fail(OLB_ERR_ARG, "null gradient outputs");
+  if ((obj != nullptr) == (u_target != nullptr))
+    return fail(OLB_ERR_ARG, "give either a plane objective or a target velocity, not both or neither");
+  if (obj) return adjoint_plane(h, n_steps, K, obj, out->loss, out->dL_dgamma, out->dL_dtau, out->dL_dF);
+  return adjoint_misfit(h, n_steps, K, u_target, region, out->loss, out->dL_dgamma, out->dL_dtau, out->dL_dF);
 }
 
 // ---------------------------------------------------------------------------------

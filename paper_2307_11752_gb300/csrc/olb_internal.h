@@ -38,13 +38,18 @@ struct HostParams {
   double omega;
   int trt;                // collision: 0 BGK, 1 TRT
   double omega_minus;     // TRT odd-part rate (from tau and the magic parameter)
+  double domega_minus;    // d omega_minus / d omega at fixed magic parameter (BGK: 1)
   double force[3];
   int forced;
   const void* gamma;      // per-cell porosity in the compute type, or nullptr
+  const void* ffield;     // per-cell force density [3][ncell] in the compute type, or nullptr
   const uint32_t* pmask;  // per cell: bit i set when x + c_i is a non-fluid cell of the lattice
   const uint32_t* word;   // per cell link word of the step kernel
   int outside_links;      // some fluid cell has a link leaving the domain
   int y0, y1, z0, z1;     // rows holding fluid cells: y in [y0, y1], z in [z0, z1]
+  unsigned* err;          // device error word of the handle (set by kernels whose bounded waits ran out)
+  unsigned inject_extra_tx;                // failure injection: bytes a TMA-fed step waits for beyond its copies
+  unsigned long long inject_wait_ns;       // and the limit of its waits then
   cudaStream_t stream;
 };
 
@@ -81,6 +86,8 @@ struct KernelTable {
   size_t lambda_elem;  // bytes per adjoint population
   cudaError_t (*step)(const HostParams&, int gather, int scatter, bool stats, const void* src,
                       void* dst, double* partials);
+  // rows of partial sums that step() with these patterns writes when stats is set
+  int64_t (*step_rows)(const HostParams&, int gather, int scatter);
   cudaError_t (*to_f64)(const HostParams&, int gather, const void* src, double* f);
   cudaError_t (*moments)(const HostParams&, int gather, const void* src, double* rho, double* u);
   cudaError_t (*stats)(const HostParams&, int gather, const void* src, double* partials);
@@ -88,12 +95,14 @@ struct KernelTable {
   cudaError_t (*init_eq)(const HostParams&, const double* rho, const double* u, void* dst);
   cudaError_t (*perturb)(const HostParams&, const double* df, void* dst);
   cudaError_t (*materialize)(const HostParams&, int gather, const void* src, void* dst);
+  // dgamma [cells] and dforce [3][cells] (either may be null) accumulate the
+  // gradients; the seeds write lam^N and the objective's own dforce term.
   cudaError_t (*adjoint)(const HostParams&, int gather, const void* state, const void* lam_in,
-                         void* lam_out, double* dgamma, double* partials);
+                         void* lam_out, double* dgamma, double* dforce, double* partials);
   cudaError_t (*loss_seed)(const HostParams&, int gather, const void* src, int axis, int index,
-                           int comp, double inv_count, void* lam, double* partials);
+                           int comp, double inv_count, void* lam, double* dforce, double* partials);
   cudaError_t (*misfit_seed)(const HostParams&, int gather, const void* src, const double* u_target,
-                             const uint8_t* region, void* lam, double* partials);
+                             const uint8_t* region, void* lam, double* dforce, double* partials);
 };
 
 // dtype: 0 f64, 1 f32, 2 f16 (shifted), 3 bf16 (shifted)
@@ -120,6 +129,17 @@ struct AdeHost {
 cudaError_t ade_step(const AdeHost& h, const void* src, void* dst);
 cudaError_t ade_init(const AdeHost& h, const double* C, void* g);
 cudaError_t ade_density(const AdeHost& h, const void* g, double* C);
+
+// Host helpers of the TMA-fed step (olb_api.cu).  SM count of the current device,
+// and a tiled tensor map (a CUtensorMap, 128 bytes at `map`) over the population
+// planes of a buffer: dimensions (x, y, z, population), box (box_x, box_rows, 1, 1).
+// Returns false when the driver does not provide the encoder or refuses the layout.
+int device_sm_count();
+// Tuning setting of the TMA-fed step: the environment variable `name` (read once)
+// when set to an integer, else `fallback` (the compiled default).
+int tma_setting(const char* name, int fallback);
+bool encode_population_map(void* map, int elem_bytes, bool bf16, const void* base, int nx, int ny, int nz, int q,
+                           int pitch, int box_x, int box_rows);
 
 // Where a caller's array lives, seen from the current device: host memory
 // (pageable or pinned), memory the current device can use (its own device

@@ -29,6 +29,7 @@
 #include <stdint.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "olb_internal.h"
 
@@ -71,6 +72,23 @@
 #endif
 #ifndef OLB_GHOST_COORDS32
 #define OLB_GHOST_COORDS32 0
+#endif
+// The pull step (two-buffer, state POST) of the paired kernel takes its populations
+// through TMA tile copies into shared memory (olb_tma.cuh) where the lattice fits;
+// tiles in flight per block for FP32 and for 16-bit storage.
+#ifndef OLB_TMA
+#define OLB_TMA 0
+#endif
+#ifndef OLB_TMA_STAGES32
+#define OLB_TMA_STAGES32 2
+#endif
+#ifndef OLB_TMA_STAGES16
+#define OLB_TMA_STAGES16 3
+#endif
+// Launch the step kernels with programmatic dependent launch (each step's grid is
+// scheduled while the previous one drains, and waits for it before touching memory).
+#ifndef OLB_PDL
+#define OLB_PDL 1
 #endif
 
 namespace olb {
@@ -132,6 +150,38 @@ constexpr int kWordMatShift = 22;
 #define OLB_SOLID_FILL 0
 #endif
 
+// Programmatic dependent launch.  A step grid launched with the programmatic
+// stream-serialization attribute can be scheduled before the previous step's grid
+// has finished.  griddepcontrol.wait blocks until every prerequisite grid has
+// completed and its memory operations are visible (it returns at once when the
+// grid was launched without the attribute), so it comes before the first global
+// access; launch_dependents then allows the next step's grid to be scheduled
+// into the SM slots this grid's blocks free as they retire.
+__device__ __forceinline__ void pdl_wait_then_release() {
+#if OLB_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+// Launch `kernel` on `stream` with `smem` bytes of dynamic shared memory, with the
+// programmatic stream-serialization attribute when OLB_PDL is on.
+template <class... Exp, class... Act>
+cudaError_t launch_step(void (*kernel)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                        Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = OLB_PDL ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Act>(args)...);
+}
+
 // ---------------------------------------------------------------------------------
 // Storage types: load/store with conversion to the compute type.
 // ---------------------------------------------------------------------------------
@@ -180,7 +230,10 @@ struct Params {
   int moving;
   C omega, half_force[3], force[3];
   C omega_minus;  // TRT: relaxation rate of the odd part (omega is the even rate)
-  int forced;
+  C domega_minus;  // TRT: d omega_minus / d omega at fixed magic parameter (BGK: 1)
+  int forced;  // a uniform force or a force field is set
+  // per-cell force density [3][ncell] in the compute type, or null (the uniform force)
+  const C* __restrict__ ffield;
   const C* __restrict__ gamma;
   // per cell: bit i set when x + c_i is a non-fluid cell of the lattice (a wall
   // link whose bounced population is stored in that cell)
@@ -212,11 +265,13 @@ Params<C> to_params(const HostParams& h) {
   p.moving = h.moving;
   p.omega = (C)h.omega;
   p.omega_minus = (C)h.omega_minus;
+  p.domega_minus = (C)h.domega_minus;
   for (int a = 0; a < 3; ++a) {
     p.force[a] = (C)h.force[a];
     p.half_force[a] = (C)(0.5 * h.force[a]);
   }
-  p.forced = h.forced;
+  p.forced = h.forced || h.ffield != nullptr;
+  p.ffield = reinterpret_cast<const C*>(h.ffield);
   p.gamma = reinterpret_cast<const C*>(h.gamma);
   p.pmask = h.pmask;
   p.word = h.word;
@@ -298,6 +353,21 @@ __device__ __forceinline__ C wall_term(const Params<C>& p, int i, int m) {
     const double* u = p.wall_u + 4 * m;
     double cu = L::c(i, 0) * u[0] + L::c(i, 1) * u[1] + L::c(i, 2) * u[2];
     return (C)(6.0 * L::w(i) * cu);
+  }
+}
+
+// Force density of a cell: the per-cell field when one is set, else the uniform force.
+template <class C>
+__device__ __forceinline__ void force_at(const Params<C>& p, int cell, C (&F)[3]) {
+  if (p.ffield) {
+    const size_t N = (size_t)p.ncell;
+    F[0] = p.ffield[cell];
+    F[1] = p.ffield[N + cell];
+    F[2] = p.ffield[2 * N + cell];
+  } else {
+    F[0] = p.force[0];
+    F[1] = p.force[1];
+    F[2] = p.force[2];
   }
 }
 
@@ -396,13 +466,13 @@ __device__ __forceinline__ void moments(const C (&f)[L::Q], C& drho, C (&j)[3]) 
 // f- at omega_minus, and the Guo source is split the same way with factors
 // (1 - omega/2) and (1 - omega_minus/2).
 template <class L, class C, bool TRT = false>
-__device__ __forceinline__ void collide(const Params<C>& p, C gamma, C (&f)[L::Q], C drho,
+__device__ __forceinline__ void collide(const Params<C>& p, C gamma, const C (&F)[3], C (&f)[L::Q], C drho,
                                         const C (&j)[3], C& rho_out, C (&u_out)[3]) {
   const C rho = C(1) + drho;
   const C inv = C(1) / rho;
   C u[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) u[d] = (j[d] + p.half_force[d]) * inv;
+  for (int d = 0; d < 3; ++d) u[d] = (j[d] + C(0.5) * F[d]) * inv;
   rho_out = rho;
   u_out[0] = u[0];
   u_out[1] = u[1];
@@ -413,7 +483,7 @@ __device__ __forceinline__ void collide(const Params<C>& p, C gamma, C (&f)[L::Q
   const C rs = C(1.5) * rho * usq;
   const C gf = C(1) - C(0.5) * om;
   C uF = C(0);
-  if (p.forced) uF = up[0] * p.force[0] + up[1] * p.force[1] + up[2] * p.force[2];
+  if (p.forced) uF = up[0] * F[0] + up[1] * F[1] + up[2] * F[2];
   {
     const C w0 = (C)L::w(0);
     C feq = w0 * (drho - rs);
@@ -429,11 +499,11 @@ __device__ __forceinline__ void collide(const Params<C>& p, C gamma, C (&f)[L::Q
     for (int d = 0; d < L::DIM; ++d) {
       if (L::c(kp, d) == 1) {
         cu += up[d];
-        cF += p.force[d];
+        cF += F[d];
       }
       if (L::c(kp, d) == -1) {
         cu -= up[d];
-        cF -= p.force[d];
+        cF -= F[d];
       }
     }
     const C sym = wk * (drho + rho * (C(4.5) * cu * cu) - rs);
@@ -626,6 +696,7 @@ __global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typena
   using C = typename Store<S>::C;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
   const int tid = threadIdx.x;
+  pdl_wait_then_release();
   const int z = p.z0 + blockIdx.z;
   const int x = (blockIdx.x << p.tile_shift) + (tid & ((1 << p.tile_shift) - 1));
   const int y = p.y0 + blockIdx.y * (256 >> p.tile_shift) + (tid >> p.tile_shift);
@@ -635,11 +706,13 @@ __global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typena
     C f[L::Q];
     gather_bulk<L, S, G>(p, src, n, f);
     const C gamma = p.gamma ? p.gamma[n.cell] : C(1);
+    C F[3];
+    force_at(p, n.cell, F);
     const bool edge = p.outside_links && on_edge<L>(p, x, y, z);
     if (edge) gather_outside<L, S, G>(p, src, n, f);
     C drho, j[3], rho, u[3];
     moments<L>(f, drho, j);
-    collide<L, C, TRT>(p, gamma, f, drho, j, rho, u);
+    collide<L, C, TRT>(p, gamma, F, f, drho, j, rho, u);
     if (w & kWordFluid) {
       const uint32_t pm = w & (kWordLinks | kWordMoving);
       const int cls = edge ? 3 : (pm ? 2 : 1);
@@ -687,12 +760,13 @@ __global__ void __launch_bounds__(256) k_moments(Params<typename Store<S>::C> p,
   if (cls != 0) {
     C f[L::Q];
     gather<L, S, G>(p, src, n, cls, f);
-    C drho, j[3];
+    C drho, j[3], F[3];
     moments<L>(f, drho, j);
+    force_at(p, n.cell, F);
     const C rho = C(1) + drho;
     r = (double)rho;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) u[d] = (double)((j[d] + p.half_force[d]) / rho);
+    for (int d = 0; d < 3; ++d) u[d] = (double)((j[d] + C(0.5) * F[d]) / rho);
   }
   if (rho_out) rho_out[n.cell] = r;
   if (u_out) {
@@ -713,12 +787,13 @@ __global__ void __launch_bounds__(256) k_stats(Params<typename Store<S>::C> p, c
     if (cls != 0) {
       C f[L::Q];
       gather<L, S, G>(p, src, n, cls, f);
-      C drho, j[3];
+      C drho, j[3], F[3];
       moments<L>(f, drho, j);
+      force_at(p, n.cell, F);
       const C rho = C(1) + drho;
       C u[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) u[d] = (j[d] + p.half_force[d]) / rho;
+      for (int d = 0; d < 3; ++d) u[d] = (j[d] + C(0.5) * F[d]) / rho;
       stats_of(drho, j, u, sv);
     }
   }
@@ -807,7 +882,17 @@ __global__ void __launch_bounds__(256) k_materialize(Params<typename Store<S>::C
 //   D = sum over moving-wall links of lam*_i (-6 w_i c_i.u_w)      (density in the wall term)
 // and the gradient contributions
 //   dL/dgamma(x) += B.u,
-//   dL/domega    += -sum lam*_k f_k + rho A - (3 m1.F - 3 m0 u'.F + 9 u'.m2.F)/2.
+//   dL/domega    += -sum lam*_k f_k + rho A - (3 m1.F - 3 m0 u'.F + 9 u'.m2.F)/2,
+//   dL/dF(x)     += (gamma/(2 rho)) B + (1 - omega/2)(3 m1 - 3 m0 u' + 9 m2 u')
+// (F(x) the cell's force density: through u = (j + F/2)/rho, and explicitly in the
+// Guo source).
+// TRT = true (the two-relaxation-time collision): the relaxation and the source act
+// on the even and odd parts of each pair (i, opp(i)) with omega+ = omega,
+// omega- = omega_minus and (1 - omega+-/2).  The even part of lam* carries m0 and
+// m2, the odd part m1, so the adjoint is the one above with omega on m1 replaced by
+// omega- (in A and B; the source's derivative holds no m1), the own-population term
+// lam*_i - omega+ lam*+_i - omega- lam*-_i, and, for dL/domega at fixed magic
+// parameter, m1 and the odd part of sum lam* f scaled by d omega- / d omega.
 // ---------------------------------------------------------------------------------
 template <class S>
 struct LambdaOf {
@@ -818,11 +903,11 @@ struct LambdaOf<double> {
   using T = double;
 };
 
-template <class L, class S, int G>
+template <class L, class S, int G, bool TRT>
 __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p, const S* state,
                                                  const typename LambdaOf<S>::T* __restrict__ lam_in,
                                                  typename LambdaOf<S>::T* __restrict__ lam_out,
-                                                 double* dgamma, double* partials) {
+                                                 double* dgamma, double* dforce, double* partials) {
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -862,10 +947,12 @@ __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p,
       const C rho = C(1) + drho;
       const C inv = C(1) / rho;
       const C gamma = p.gamma ? p.gamma[n.cell] : C(1);
+      C F[3];
+      force_at(p, n.cell, F);
       C u[3], up[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        u[d] = (j[d] + p.half_force[d]) * inv;
+        u[d] = (j[d] + C(0.5) * F[d]) * inv;
         up[d] = gamma * u[d];
       }
       // moments of mu_k = w_k lam*_k
@@ -895,11 +982,12 @@ __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p,
         for (int b = 0; b < a; ++b) m2[a][b] = m2[b][a];
       const C om = p.omega;
       const C gf = C(1) - C(0.5) * om;
+      const C om_odd = TRT ? p.omega_minus : om;  // relaxation rate of the odd part (m1)
       C m2u[3], m2F[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         m2u[a] = m2[a][0] * up[0] + m2[a][1] * up[1] + m2[a][2] * up[2];
-        m2F[a] = m2[a][0] * p.force[0] + m2[a][1] * p.force[1] + m2[a][2] * p.force[2];
+        m2F[a] = m2[a][0] * F[0] + m2[a][1] * F[1] + m2[a][2] * F[2];
       }
       const C usq = up[0] * up[0] + up[1] * up[1] + up[2] * up[2];
       const C m1u = m1[0] * up[0] + m1[1] * up[1] + m1[2] * up[2];
@@ -909,12 +997,21 @@ __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p,
       const C A = m0 + Aex;
       C B[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-        B[a] = om * rho * (C(3) * m1[a] + C(9) * m2u[a] - C(3) * m0 * up[a]) +
-               gf * (C(9) * m2F[a] - C(3) * m0 * p.force[a]);
+      for (int a = 0; a < 3; ++a) {
+        if constexpr (TRT)
+          B[a] = rho * (om_odd * C(3) * m1[a] + om * (C(9) * m2u[a] - C(3) * m0 * up[a])) +
+                 gf * (C(9) * m2F[a] - C(3) * m0 * F[a]);
+        else
+          B[a] = om * rho * (C(3) * m1[a] + C(9) * m2u[a] - C(3) * m0 * up[a]) +
+                 gf * (C(9) * m2F[a] - C(3) * m0 * F[a]);
+      }
       const C Bu = B[0] * u[0] + B[1] * u[1] + B[2] * u[2];
       const C gi = gamma * inv;
-      const C base = om * A - gi * Bu + direct;
+      C base;
+      if constexpr (TRT)
+        base = om * (m0 + C(4.5) * um2u - C(1.5) * m0 * usq) + om_odd * C(3) * m1u - gi * Bu + direct;
+      else
+        base = om * A - gi * Bu + direct;
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         C Bc = C(0);
@@ -923,29 +1020,62 @@ __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p,
           if (L::c(i, a) == 1) Bc += B[a];
           if (L::c(i, a) == -1) Bc -= B[a];
         }
-        lam_out[i * N + n.cell] = (typename LambdaOf<S>::T)((C(1) - om) * ls[i] + base + gi * Bc);
+        C own;
+        if constexpr (TRT) {
+          // lam*_i - omega+ (lam*_i + lam*_opp)/2 - omega- (lam*_i - lam*_opp)/2
+          const C lo = ls[opp<L>(i)];
+          own = ls[i] - om * (C(0.5) * (ls[i] + lo)) - om_odd * (C(0.5) * (ls[i] - lo));
+        } else {
+          own = (C(1) - om) * ls[i];
+        }
+        lam_out[i * N + n.cell] = (typename LambdaOf<S>::T)(own + base + gi * Bc);
       }
       if (dgamma) dgamma[n.cell] += (double)Bu;
+      if (dforce) {
+        // through u = (j + F/2)/rho (B gamma / (2 rho)) and the Guo source's own F;
+        // TRT: the source's odd part (m1) carries 1 - omega-/2
+        const C gf_odd = TRT ? C(1) - C(0.5) * om_odd : gf;
+        const C hg = C(0.5) * gi;
+#pragma unroll
+        for (int a = 0; a < L::DIM; ++a)
+          dforce[(size_t)a * p.ncell + n.cell] +=
+              (double)(hg * B[a] + gf_odd * C(3) * m1[a] + gf * (C(9) * m2u[a] - C(3) * m0 * up[a]));
+      }
       // dL/domega = sum_k lam*_k (feq_k - f_k) - G/2.  feq and f are both O(w) and
       // differ by the small non-equilibrium part, so the O(w) parts are removed
       // analytically before rounding: sum lam* (feq - w) = m0 drho + rho (A - m0)
       // and sum lam* (f - w) = lf (f stored shifted).
-      const C m1F = m1[0] * p.force[0] + m1[1] * p.force[1] + m1[2] * p.force[2];
-      const C uF = up[0] * p.force[0] + up[1] * p.force[1] + up[2] * p.force[2];
+      const C m1F = m1[0] * F[0] + m1[1] * F[1] + m1[2] * F[2];
+      const C uF = up[0] * F[0] + up[1] * F[1] + up[2] * F[2];
       const C uM2F = up[0] * m2F[0] + up[1] * m2F[1] + up[2] * m2F[2];
-      const C src_moment = C(3) * m1F - C(3) * m0 * uF + C(9) * uM2F;
-      sv[0] = m0 * drho + rho * Aex - lf - C(0.5) * src_moment;
+      if constexpr (TRT) {
+        // the odd parts (m1 and the odd part of sum lam* f) move with omega- (omega)
+        const C dwm = p.domega_minus;
+        C lf_odd = C(0);
+#pragma unroll
+        for (int k = 1; k <= L::HALF; ++k)
+          lf_odd += C(0.5) * (ls[k] - ls[k + L::HALF]) * (f[k] - f[k + L::HALF]);
+        const C src_w = C(3) * dwm * m1F - C(3) * m0 * uF + C(9) * uM2F;
+        const C Aex_w = C(3) * dwm * m1u + C(4.5) * um2u - C(1.5) * m0 * usq;
+        sv[0] = m0 * drho + rho * Aex_w - (lf - lf_odd) - dwm * lf_odd - C(0.5) * src_w;
+      } else {
+        const C src_moment = C(3) * m1F - C(3) * m0 * uF + C(9) * uM2F;
+        sv[0] = m0 * drho + rho * Aex - lf - C(0.5) * src_moment;
+      }
     }
   }
   block_reduce_row(sv, partials + 8 * block_linear(), true);
 }
 
 // Objective (mean u[comp] over fluid cells of a plane) and its gradient seed
-// lam^N_i(x) = (c_i[comp] - u[comp]) / (rho M) on those cells, 0 elsewhere.
+// lam^N_i(x) = (c_i[comp] - u[comp]) / (rho M) on those cells, 0 elsewhere.  With
+// dforce: dL/dF(x) starts at the objective's own term 1/(2 rho M) on component comp
+// of those cells (u = (j + F/2)/rho) and 0 elsewhere.
 template <class L, class S, int G>
 __global__ void __launch_bounds__(256) k_loss_seed(Params<typename Store<S>::C> p, const S* src, int axis,
                                                    int index, int comp, double inv_count,
-                                                   typename LambdaOf<S>::T* lam, double* partials) {
+                                                   typename LambdaOf<S>::T* lam, double* dforce,
+                                                   double* partials) {
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -961,8 +1091,10 @@ __global__ void __launch_bounds__(256) k_loss_seed(Params<typename Store<S>::C> 
       C drho, j[3];
       moments<L>(f, drho, j);
       const C rho = C(1) + drho;
+      C F[3];
+      force_at(p, n.cell, F);
       const C jc = comp == 0 ? j[0] : (comp == 1 ? j[1] : j[2]);
-      const C fc = comp == 0 ? p.half_force[0] : (comp == 1 ? p.half_force[1] : p.half_force[2]);
+      const C fc = C(0.5) * (comp == 0 ? F[0] : (comp == 1 ? F[1] : F[2]));
       const C uc = (jc + fc) / rho;
       sv[0] = uc;
       const C scale = (C)inv_count / rho;
@@ -971,9 +1103,18 @@ __global__ void __launch_bounds__(256) k_loss_seed(Params<typename Store<S>::C> 
         const int ci = comp == 0 ? L::c(i, 0) : (comp == 1 ? L::c(i, 1) : L::c(i, 2));
         lam[i * N + n.cell] = (typename LambdaOf<S>::T)(((C)ci - uc) * scale);
       }
+      if (dforce) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          dforce[(size_t)a * p.ncell + n.cell] = a == comp ? (double)(C(0.5) * scale) : 0.0;
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) lam[i * N + n.cell] = 0;
+      if (dforce) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dforce[(size_t)a * p.ncell + n.cell] = 0.0;
+      }
     }
   }
   block_reduce_row(sv, partials + 8 * block_linear(), false);
@@ -988,7 +1129,8 @@ __global__ void __launch_bounds__(256) k_loss_seed(Params<typename Store<S>::C> 
 template <class L, class S, int G>
 __global__ void __launch_bounds__(256) k_misfit_seed(Params<typename Store<S>::C> p, const S* src,
                                                      const double* u_target, const uint8_t* region,
-                                                     typename LambdaOf<S>::T* lam, double* partials) {
+                                                     typename LambdaOf<S>::T* lam, double* dforce,
+                                                     double* partials) {
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1004,10 +1146,12 @@ __global__ void __launch_bounds__(256) k_misfit_seed(Params<typename Store<S>::C
       moments<L>(f, drho, j);
       const C rho = C(1) + drho;
       const C inv = C(1) / rho;
+      C F[3];
+      force_at(p, n.cell, F);
       C u[3], e[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        u[a] = (j[a] + p.half_force[a]) * inv;
+        u[a] = (j[a] + C(0.5) * F[a]) * inv;
         e[a] = a < L::DIM ? u[a] - (C)u_target[(size_t)a * p.ncell + n.cell] : C(0);
         sv[0] += C(0.5) * e[a] * e[a];
       }
@@ -1019,9 +1163,18 @@ __global__ void __launch_bounds__(256) k_misfit_seed(Params<typename Store<S>::C
         const C ec = L::c(i, 0) * e[0] + L::c(i, 1) * e[1] + L::c(i, 2) * e[2];
         lam[i * N + n.cell] = (typename LambdaOf<S>::T)((ec - eu) * inv);
       }
+      // dJ/dF(x) from the objective itself: e / (2 rho)
+      if (dforce) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dforce[(size_t)a * p.ncell + n.cell] = (double)(C(0.5) * e[a] * inv);
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) lam[i * N + n.cell] = 0;
+      if (dforce) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dforce[(size_t)a * p.ncell + n.cell] = 0.0;
+      }
     }
   }
   block_reduce_row(sv, partials + 8 * block_linear(), false);
@@ -1030,6 +1183,7 @@ __global__ void __launch_bounds__(256) k_misfit_seed(Params<typename Store<S>::C
 }  // namespace olb
 
 #include "olb_pair.cuh"
+#include "olb_tma.cuh"
 
 namespace olb {
 
@@ -1047,10 +1201,158 @@ struct Launch {
     return p;
   }
 
+  template <class PL>
+  static void fill_planes(PL& pl, const void* src, void* dst, int pitch) {
+    for (int i = 0; i < 19; ++i) {
+      const int k = i < L::Q ? i : 0;
+      pl.src[i] = static_cast<const S*>(src) + (size_t)k * pitch;
+      pl.dst[i] = static_cast<S*>(dst) + (size_t)k * pitch;
+    }
+  }
+
+  // Tile geometry of the TMA-fed pull step; false when the lattice does not fit it
+  // (double storage, odd nx, a force field, nx > 512 or rows not a 16-byte multiple).
+  static bool tma_geometry(const HostParams& h, TmaGeom& g) {
+    if constexpr (std::is_same<S, double>::value) {
+      return false;
+    } else {
+      if (!tma_setting("OLB_TMA", OLB_TMA) || !pairs_ok(h.nx) || h.ffield != nullptr || h.err == nullptr ||
+          h.nx > 512)
+        return false;
+      const int e = (int)sizeof(S);
+      const int nbx = h.nx <= 256 ? 1 : 2;
+      const int bx = h.nx / nbx;
+      // copy starts: x * elem a 16-byte multiple; shared destinations of the second
+      // x box and of single rows (periodic y) 128-byte aligned
+      if (nbx * bx != h.nx || (bx * e) % 16 != 0) return false;
+      if (nbx == 2 && (bx * e) % 128 != 0) return false;
+      if ((h.periodic & 2u) && (h.nx * e) % 128 != 0) return false;
+      g.pairs = h.nx / 2;
+      g.rows = 256 / g.pairs;
+      if (g.rows < 1 || (nbx == 2 && g.rows != 1)) return false;
+      g.nbx = nbx;
+      g.bx = bx;
+      const int ny_box = h.y1 - h.y0 + 1, nz_box = h.z1 - h.z0 + 1;
+      if (ny_box < 1 || nz_box < 1) return false;
+      g.tiles_y = (ny_box + g.rows - 1) / g.rows;
+      g.ntiles = g.tiles_y * nz_box;
+      g.stages = e == 4 ? tma_setting("OLB_TMA_STAGES32", OLB_TMA_STAGES32)
+                        : tma_setting("OLB_TMA_STAGES16", OLB_TMA_STAGES16);
+      if (g.stages < 2 || g.stages > kTmaMaxStages) return false;
+      g.stage_bytes = (unsigned)(L::Q * g.rows * h.nx * e);
+      g.box_slot = (unsigned)((g.rows * h.nx * e + 127) / 128 * 128);
+      g.err = h.err;
+      g.extra_tx = h.inject_extra_tx;
+      g.wait_ns = h.inject_extra_tx ? h.inject_wait_ns : kTmaWaitNs;
+      return true;
+    }
+  }
+  static size_t tma_smem(const TmaGeom& g) {
+    return kTmaAlignSlack + kTmaBarrierBytes + (size_t)g.stages * L::Q * g.box_slot;
+  }
+
+  // Blocks of the persistent TMA grid: resident blocks per SM times SMs, at most one
+  // per tile (0: the kernel cannot run with this shared memory).
+  template <bool STATS, bool WALLS, bool TRT>
+  static int tma_blocks(const TmaGeom& g, size_t smem) {
+    if constexpr (std::is_same<S, double>::value) {
+      return 0;
+    } else {
+      auto kernel = k_step_pair_tma<L, S, STATS, WALLS, TRT>;
+      // per instance: the shared-memory size last configured and its occupancy
+      static thread_local size_t set_bytes = 0;
+      static thread_local int per_sm = 0, sms = 0;
+      if (set_bytes != smem) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess) {
+          cudaGetLastError();
+          set_bytes = 0;
+          return 0;
+        }
+        sms = device_sm_count();
+        set_bytes = smem;
+      }
+      return std::min(per_sm * sms, g.ntiles);
+    }
+  }
+
+  template <bool STATS, bool WALLS, bool TRT>
+  static cudaError_t launch_tma(const HostParams& h, const TmaGeom& tg, int blocks, const void* src, void* dst,
+                                double* partials) {
+    if constexpr (std::is_same<S, double>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      // the tensor maps of the last few source buffers (a lattice alternates two)
+      struct MapEntry {
+        const void* src = nullptr;
+        int nx = 0, ny = 0, nz = 0, pitch = 0, bx = 0, rows = 0;
+        alignas(64) CUtensorMap tmain, trow;
+      };
+      static thread_local MapEntry cache[4];
+      static thread_local int next = 0;
+      MapEntry* e = nullptr;
+      for (auto& c : cache)
+        if (c.src == src && c.nx == h.nx && c.ny == h.ny && c.nz == h.nz && c.pitch == h.pitch && c.bx == tg.bx &&
+            c.rows == tg.rows)
+          e = &c;
+      if (!e) {
+        e = &cache[next];
+        next = (next + 1) % 4;
+        const bool bf = std::is_same<S, __nv_bfloat16>::value;
+        e->src = nullptr;
+        if (!encode_population_map(&e->tmain, (int)sizeof(S), bf, src, h.nx, h.ny, h.nz, L::Q, h.pitch, tg.bx,
+                                   tg.rows) ||
+            !encode_population_map(&e->trow, (int)sizeof(S), bf, src, h.nx, h.ny, h.nz, L::Q, h.pitch, tg.bx, 1))
+          return cudaErrorInvalidValue;
+        e->src = src;
+        e->nx = h.nx;
+        e->ny = h.ny;
+        e->nz = h.nz;
+        e->pitch = h.pitch;
+        e->bx = tg.bx;
+        e->rows = tg.rows;
+      }
+      Params<float> p = params(h);
+      Planes<S, WALLS> pl;
+      if constexpr (WALLS) pl.lead = 0;
+      fill_planes(pl, src, dst, h.pitch);
+      return launch_step(k_step_pair_tma<L, S, STATS, WALLS, TRT>, dim3(blocks), dim3(256), tma_smem(tg), h.stream, p,
+                         pl, e->tmain, e->trow, tg, partials);
+    }
+  }
+
+  template <bool STATS, bool TRT>
+  static int tma_blocks_for(const HostParams& h, const TmaGeom& tg) {
+    const size_t smem = tma_smem(tg);
+    if (h.cls == nullptr && !OLB_FORCE_WALLS) return tma_blocks<STATS, false, TRT>(tg, smem);
+    return tma_blocks<STATS, true, TRT>(tg, smem);
+  }
+
+  // Rows of partial sums that step() with these patterns writes when stats is set.
+  static int64_t step_rows(const HostParams& h, int gather, int scatter) {
+    TmaGeom tg;
+    if (gather == G_PULL && scatter == S_OWN && tma_geometry(h, tg)) {
+      const int b = h.trt ? tma_blocks_for<true, true>(h, tg) : tma_blocks_for<true, false>(h, tg);
+      if (b >= 1) return b;
+    }
+    return make_step_grid(h, !std::is_same<S, double>::value && pairs_ok(h.nx) && h.ffield == nullptr).blocks();
+  }
+
   template <int G, int SC, bool STATS, bool TRT>
   static cudaError_t step_t(const HostParams& h, const void* src, void* dst, double* partials) {
+    if constexpr (!std::is_same<S, double>::value && G == G_PULL && SC == S_OWN) {
+      TmaGeom tg;
+      if (tma_geometry(h, tg)) {
+        const int blocks = tma_blocks_for<STATS, TRT>(h, tg);
+        if (blocks >= 1) {
+          if (h.cls == nullptr && !OLB_FORCE_WALLS)
+            return launch_tma<STATS, false, TRT>(h, tg, blocks, src, dst, partials);
+          return launch_tma<STATS, true, TRT>(h, tg, blocks, src, dst, partials);
+        }
+      }
+    }
     if constexpr (!std::is_same<S, double>::value) {
-      if (pairs_ok(h.nx)) {
+      if (pairs_ok(h.nx) && h.ffield == nullptr) {  // the paired kernel takes a uniform force
         const StepGrid g = make_step_grid(h, true);
         Params<float> p = params(h);
         p.gx = g.gx;
@@ -1066,20 +1368,19 @@ struct Launch {
         if (h.cls == nullptr && !OLB_FORCE_WALLS) {  // all fluid, all periodic
           Planes<S, false> pl;
           fill(pl);
-          k_step_pair<L, S, G, SC, STATS, false, TRT><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
-        } else {
-          Planes<S, true> pl;
-          pl.lead = 0;
-          fill(pl);
-          k_step_pair<L, S, G, SC, STATS, true, TRT><<<g.dims(), 256, 0, h.stream>>>(p, pl, partials);
+          return launch_step(k_step_pair<L, S, G, SC, STATS, false, TRT>, g.dims(), dim3(256), 0, h.stream, p, pl,
+                             partials);
         }
-        return cudaGetLastError();
+        Planes<S, true> pl;
+        pl.lead = 0;
+        fill(pl);
+        return launch_step(k_step_pair<L, S, G, SC, STATS, true, TRT>, g.dims(), dim3(256), 0, h.stream, p, pl,
+                           partials);
       }
     }
     const StepGrid g = make_step_grid(h, false);
-    k_step<L, S, G, SC, STATS, TRT><<<g.dims(), 256, 0, h.stream>>>(
-        params(h), static_cast<const S*>(src), static_cast<S*>(dst), partials);
-    return cudaGetLastError();
+    return launch_step(k_step<L, S, G, SC, STATS, TRT>, g.dims(), dim3(256), 0, h.stream, params(h),
+                       static_cast<const S*>(src), static_cast<S*>(dst), partials);
   }
   template <int G, int SC>
   static cudaError_t step_s(const HostParams& h, bool stats, const void* src, void* dst,
@@ -1133,23 +1434,40 @@ struct Launch {
     OLB_BY_GATHER(k_materialize, static_cast<const S*>(src), static_cast<S*>(dst));
   }
   static cudaError_t loss_seed(const HostParams& h, int gather, const void* src, int axis,
-                               int index, int comp, double inv_count, void* lam,
+                               int index, int comp, double inv_count, void* lam, double* dforce,
                                double* partials) {
     OLB_BY_GATHER(k_loss_seed, static_cast<const S*>(src), axis, index, comp, inv_count,
-                  static_cast<T*>(lam), partials);
+                  static_cast<T*>(lam), dforce, partials);
   }
   static cudaError_t misfit_seed(const HostParams& h, int gather, const void* src, const double* u_target,
-                                 const uint8_t* region, void* lam, double* partials) {
-    OLB_BY_GATHER(k_misfit_seed, static_cast<const S*>(src), u_target, region, static_cast<T*>(lam), partials);
-  }
-  static cudaError_t adjoint(const HostParams& h, int gather, const void* state,
-                             const void* lam_in, void* lam_out, double* dgamma,
-                             double* partials) {
-    if (gather == G_PULL_SWAP) return cudaErrorInvalidValue;
-    OLB_BY_GATHER(k_adjoint, static_cast<const S*>(state), static_cast<const T*>(lam_in),
-                  static_cast<T*>(lam_out), dgamma, partials);
+                                 const uint8_t* region, void* lam, double* dforce, double* partials) {
+    OLB_BY_GATHER(k_misfit_seed, static_cast<const S*>(src), u_target, region, static_cast<T*>(lam), dforce,
+                  partials);
   }
 #undef OLB_BY_GATHER
+  template <bool TRT>
+  static cudaError_t adjoint_t(const HostParams& h, int gather, const void* state, const void* lam_in,
+                               void* lam_out, double* dgamma, double* dforce, double* partials) {
+    Grid g = make_grid(h.nx, h.ny, h.nz);
+    const S* st = static_cast<const S*>(state);
+    const T* li = static_cast<const T*>(lam_in);
+    T* lo = static_cast<T*>(lam_out);
+    if (gather == G_OWN)
+      k_adjoint<L, S, G_OWN, TRT><<<g.grid, g.block, 0, h.stream>>>(params(h), st, li, lo, dgamma, dforce,
+                                                                      partials);
+    else if (gather == G_PULL)
+      k_adjoint<L, S, G_PULL, TRT><<<g.grid, g.block, 0, h.stream>>>(params(h), st, li, lo, dgamma, dforce,
+                                                                       partials);
+    else
+      return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
+  static cudaError_t adjoint(const HostParams& h, int gather, const void* state,
+                             const void* lam_in, void* lam_out, double* dgamma, double* dforce,
+                             double* partials) {
+    return h.trt ? adjoint_t<true>(h, gather, state, lam_in, lam_out, dgamma, dforce, partials)
+                 : adjoint_t<false>(h, gather, state, lam_in, lam_out, dgamma, dforce, partials);
+  }
 
   static cudaError_t from_f64(const HostParams& h, const double* f, void* dst) {
     Grid g = make_grid(h.nx, h.ny, h.nz);
@@ -1168,7 +1486,7 @@ struct Launch {
   }
 
   static const KernelTable* table() {
-    static const KernelTable t = {L::Q,       sizeof(S), sizeof(T), &step,    &to_f64,
+    static const KernelTable t = {L::Q,       sizeof(S), sizeof(T), &step,    &step_rows, &to_f64,
                                   &moments,   &stats,    &from_f64, &init_eq, &perturb,
                                   &materialize, &adjoint, &loss_seed, &misfit_seed};
     return &t;

@@ -341,6 +341,188 @@ __device__ __forceinline__ void ghost_stores(const Params<float>& p, const P& pl
 }
 
 // ---------------------------------------------------------------------------------
+// Everything after the population loads of one pair (x0, x0 + 1) of the step kernels:
+// bounce-back at the domain edge (own-slot loads), collision, own-slot and
+// bounce-back stores, statistics.  w: the cells' link words; f: f(t) of both cells
+// (scaled shifted values); sv: the thread's statistics accumulators.
+// ---------------------------------------------------------------------------------
+template <class L, class S, int G, int SC, bool STATS, bool WALLS, bool TRT, class P>
+__device__ __forceinline__ void pair_update(const Params<float>& p, const P& pl, const PairNbr& n, int x0, int y,
+                                            int z, const uint32_t (&w)[2], F2 gamma, F2 (&f)[L::Q],
+                                            float (&sv)[8]) {
+  constexpr int SC_NUM = (int)PairStore<S>::SCALE;
+  constexpr float INV_SCALE = 1.0f / PairStore<S>::SCALE;
+  const int cell = n.cell();
+  // links leaving the domain (no cell holds their bounce-back value)
+  bool edge[2] = {false, false};
+  if (WALLS && G != G_OWN && p.outside_links) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      Nbr c1;
+      c1.x = x0 + h;
+      c1.y = y;
+      c1.z = z;
+      edge[h] = on_edge<L>(p, x0 + h, y, z);
+      if (edge[h]) {
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+          if (outside(p, c1, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2))) {
+            const int own = (G == G_PULL) ? opp<L>(i) : i;
+            const float v = PairStore<S>::ld1(pl.src[own] + cell + h);
+            if (h == 0) f[i].v.x = v; else f[i].v.y = v;
+          }
+        }
+      }
+    }
+  }
+  F2 drho, j[3], rho, u[3];
+  collide_pair<L, SC_NUM, TRT>(p, gamma, f, drho, j, rho, u);
+  const bool fl0 = (w[0] & kWordFluid) != 0, fl1 = (w[1] & kWordFluid) != 0;
+  if (!WALLS) {
+    // every cell fluid, every axis periodic: plain paired stores only
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if (SC == S_PUSH)
+        st_pair(pl.dst[i], n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
+      else
+        PairStore<S>::st2(pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell, f[i]);
+    }
+  } else if (SC == S_OWN || SC == S_OWN_SWAP) {
+    // Own slots, one paired store per population.  A non-fluid cell's slots hold
+    // nothing except its bounce-back slots (written by fluid neighbours, bits nb):
+    // a pair whose non-fluid cell has bounce-back slots only on the side of its
+    // fluid partner (the usual case at a wall on an x face) still stores in pairs,
+    // except for the 5 directions that point from the non-fluid cell into its
+    // partner, which store the fluid cell alone.
+    const uint32_t nb0 = w[0] & kWordLinks, nb1 = w[1] & kWordLinks;
+    const bool lo = OLB_XWALL_PAIRS && !fl0 && fl1 && !(nb0 & ~dir_mask<L>(1));   // non-fluid x0, fluid x0 + 1
+    const bool hi = OLB_XWALL_PAIRS && fl0 && !fl1 && !(nb1 & ~dir_mask<L>(-1));  // fluid x0, non-fluid x0 + 1
+    // Bounce-back links: the bounced population goes into the wall cell x + c_i,
+    // in the slot that x reads there at the next step.  A cell next to a wall on
+    // an x face has its links only among the 5 directions with c_x = -1 (or +1);
+    // it tests only those.  These slots are never among the own slots stored
+    // below (see above), so the bounce-back stores go first: the own-slot stores
+    // then release the post-collision values one by one.
+    const uint32_t l0 = fl0 ? nb0 : 0u;
+    const uint32_t l1 = fl1 ? nb1 : 0u;
+    auto bounce_back = [&]() {
+    if (l0 | l1) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t l = h == 0 ? l0 : l1;
+        if (l) {
+          float fh[L::Q];
+#pragma unroll
+          for (int i = 0; i < L::Q; ++i) fh[i] = h == 0 ? f[i].v.x : f[i].v.y;
+          const float rh = h == 0 ? rho.v.x : rho.v.y;
+          if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(-1)))
+            ghost_stores<L, S, SC, -1, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
+          else if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(1)))
+            ghost_stores<L, S, SC, 1, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
+          else
+            ghost_stores<L, S, SC, 0, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
+        }
+      }
+    }
+    };
+    if (PairStore<S>::GHOST_FIRST) bounce_back();
+    if ((fl0 && fl1) || lo || hi) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        S* q = pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell;
+        if (L::c(i, 0) == 1 && lo) {
+          PairStore<S>::st1(q + 1, f[i].v.y);
+        } else if (L::c(i, 0) == -1 && hi) {
+          PairStore<S>::st1(q, f[i].v.x);
+        } else {
+          PairStore<S>::st2(q, f[i]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        S* q = pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell;
+        if (fl0) PairStore<S>::st1(q, f[i].v.x);
+        if (fl1) PairStore<S>::st1(q + 1, f[i].v.y);
+      }
+    }
+    if (!PairStore<S>::GHOST_FIRST) bounce_back();
+    if (OLB_SOLID_FILL) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!(h == 0 ? fl0 : fl1)) {
+          const uint32_t nb = w[h] & kWordLinks;
+#pragma unroll
+          for (int k = 0; k < L::Q; ++k) {
+            const int b = (SC == S_OWN) ? k : opp<L>(k);
+            if (k == 0 || !(nb & (1u << b))) PairStore<S>::st1(pl.dst[k] + cell + h, 0.0f);
+          }
+        }
+      }
+    }
+  } else {  // S_PUSH
+    const bool plain = fl0 && fl1 && !((w[0] | w[1]) & (kWordLinks | kWordMoving)) && !edge[0] && !edge[1];
+    if (plain) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) st_pair(pl.dst[i], n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
+    } else {
+      // per cell, with bounce-back links, domain edges and non-fluid cells
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t wd = w[h];
+        const int c = cell + h;
+        const float rh = h == 0 ? rho.v.x : rho.v.y;
+        Nbr c1;
+        c1.x = x0 + h;
+        c1.y = y;
+        c1.z = z;
+        if (wd & kWordFluid) {
+#pragma unroll
+          for (int i = 0; i < L::Q; ++i) {
+            const float fi = h == 0 ? f[i].v.x : f[i].v.y;
+            const int tx = 1 + h + L::c(i, 0);
+            const bool wall = i != 0 && (wd & (1u << i));
+            const bool out = i != 0 && edge[h] && outside(p, c1, L::c(i, 0), L::c(i, 1), L::c(i, 2));
+            if (wall || out) {
+              float bounced = fi;
+              float t;
+              if (wall && (wd & kWordMoving) &&
+                  moving_term<L>(p, n.at(tx, L::c(i, 1), L::c(i, 2)), i, wd, t))
+                bounced -= rh * t;
+              PairStore<S>::st1(pl.dst[opp<L>(i)] + c, bounced);
+            } else {
+              PairStore<S>::st1(pl.dst[i] + n.at(tx, L::c(i, 1), L::c(i, 2)), fi);
+            }
+          }
+        } else if (OLB_SOLID_FILL) {
+          const uint32_t nb = wd & kWordLinks;
+#pragma unroll
+          for (int k = 0; k < L::Q; ++k)
+            if (k == 0 || !(nb & (1u << opp<L>(k)))) PairStore<S>::st1(pl.dst[k] + c, 0.0f);
+        }
+      }
+    }
+  }
+  if (STATS) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (w[h] & kWordFluid) {
+        const float dr = (h == 0 ? drho.v.x : drho.v.y) * INV_SCALE;
+        float jv[3], uv[3], v[8];
+#pragma unroll
+        for (int dd = 0; dd < 3; ++dd) {
+          jv[dd] = (h == 0 ? j[dd].v.x : j[dd].v.y) * INV_SCALE;
+          uv[dd] = h == 0 ? u[dd].v.x : u[dd].v.y;
+        }
+        stats_of(dr, jv, uv, v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sv[k] = (k == 5) ? fmaxf(sv[k], v[k]) : sv[k] + v[k];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // The paired step kernel (patterns as in k_step, see scatter for the bounce-back
 // storage rules).  Requires nx even; tiles of (2 << tile_shift) cells along x by
 // (256 >> tile_shift) rows.  WALLS = false is the instance for lattices whose cells
@@ -351,10 +533,9 @@ template <class L, class S, int G, int SC, bool STATS, bool WALLS, bool TRT>
 __global__ void __launch_bounds__(256, WALLS ? PairStore<S>::MIN_BLOCKS_WALLS : PairStore<S>::MIN_BLOCKS) k_step_pair(Params<float> p,
                                                                              const __grid_constant__ Planes<S, WALLS> pl,
                                                                              double* partials) {
-  constexpr int SC_NUM = (int)PairStore<S>::SCALE;
-  constexpr float INV_SCALE = 1.0f / PairStore<S>::SCALE;
   float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int tid = threadIdx.x;
+  pdl_wait_then_release();
   int x0, y, z;
   bool active;
   {
@@ -383,173 +564,7 @@ __global__ void __launch_bounds__(256, WALLS ? PairStore<S>::MIN_BLOCKS_WALLS : 
     }
     F2 gamma(1.0f);
     if (p.gamma) gamma = F2(*reinterpret_cast<const float2*>(p.gamma + cell));
-    // links leaving the domain (no cell holds their bounce-back value)
-    bool edge[2] = {false, false};
-    if (WALLS && G != G_OWN && p.outside_links) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        Nbr c1;
-        c1.x = x0 + h;
-        c1.y = y;
-        c1.z = z;
-        edge[h] = on_edge<L>(p, x0 + h, y, z);
-        if (edge[h]) {
-#pragma unroll
-          for (int i = 1; i < L::Q; ++i) {
-            if (outside(p, c1, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2))) {
-              const int own = (G == G_PULL) ? opp<L>(i) : i;
-              const float v = PairStore<S>::ld1(pl.src[own] + cell + h);
-              if (h == 0) f[i].v.x = v; else f[i].v.y = v;
-            }
-          }
-        }
-      }
-    }
-    F2 drho, j[3], rho, u[3];
-    collide_pair<L, SC_NUM, TRT>(p, gamma, f, drho, j, rho, u);
-    const bool fl0 = (w[0] & kWordFluid) != 0, fl1 = (w[1] & kWordFluid) != 0;
-    if (!WALLS) {
-      // every cell fluid, every axis periodic: plain paired stores only
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        if (SC == S_PUSH)
-          st_pair(pl.dst[i], n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
-        else
-          PairStore<S>::st2(pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell, f[i]);
-      }
-    } else if (SC == S_OWN || SC == S_OWN_SWAP) {
-      // Own slots, one paired store per population.  A non-fluid cell's slots hold
-      // nothing except its bounce-back slots (written by fluid neighbours, bits nb):
-      // a pair whose non-fluid cell has bounce-back slots only on the side of its
-      // fluid partner (the usual case at a wall on an x face) still stores in pairs,
-      // except for the 5 directions that point from the non-fluid cell into its
-      // partner, which store the fluid cell alone.
-      const uint32_t nb0 = w[0] & kWordLinks, nb1 = w[1] & kWordLinks;
-      const bool lo = OLB_XWALL_PAIRS && !fl0 && fl1 && !(nb0 & ~dir_mask<L>(1));   // non-fluid x0, fluid x0 + 1
-      const bool hi = OLB_XWALL_PAIRS && fl0 && !fl1 && !(nb1 & ~dir_mask<L>(-1));  // fluid x0, non-fluid x0 + 1
-      // Bounce-back links: the bounced population goes into the wall cell x + c_i,
-      // in the slot that x reads there at the next step.  A cell next to a wall on
-      // an x face has its links only among the 5 directions with c_x = -1 (or +1);
-      // it tests only those.  These slots are never among the own slots stored
-      // below (see above), so the bounce-back stores go first: the own-slot stores
-      // then release the post-collision values one by one.
-      const uint32_t l0 = fl0 ? nb0 : 0u;
-      const uint32_t l1 = fl1 ? nb1 : 0u;
-      auto bounce_back = [&]() {
-      if (l0 | l1) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t l = h == 0 ? l0 : l1;
-          if (l) {
-            float fh[L::Q];
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) fh[i] = h == 0 ? f[i].v.x : f[i].v.y;
-            const float rh = h == 0 ? rho.v.x : rho.v.y;
-            if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(-1)))
-              ghost_stores<L, S, SC, -1, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
-            else if (OLB_XWALL_PAIRS && !(l & ~dir_mask<L>(1)))
-              ghost_stores<L, S, SC, 1, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
-            else
-              ghost_stores<L, S, SC, 0, PairStore<S>::GHOST_COORDS>(p, pl, n, h, y, z, l, w[h], fh, rh);
-          }
-        }
-      }
-      };
-      if (PairStore<S>::GHOST_FIRST) bounce_back();
-      if ((fl0 && fl1) || lo || hi) {
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-          S* q = pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell;
-          if (L::c(i, 0) == 1 && lo) {
-            PairStore<S>::st1(q + 1, f[i].v.y);
-          } else if (L::c(i, 0) == -1 && hi) {
-            PairStore<S>::st1(q, f[i].v.x);
-          } else {
-            PairStore<S>::st2(q, f[i]);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-          S* q = pl.dst[(SC == S_OWN) ? i : opp<L>(i)] + cell;
-          if (fl0) PairStore<S>::st1(q, f[i].v.x);
-          if (fl1) PairStore<S>::st1(q + 1, f[i].v.y);
-        }
-      }
-      if (!PairStore<S>::GHOST_FIRST) bounce_back();
-      if (OLB_SOLID_FILL) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (!(h == 0 ? fl0 : fl1)) {
-            const uint32_t nb = w[h] & kWordLinks;
-#pragma unroll
-            for (int k = 0; k < L::Q; ++k) {
-              const int b = (SC == S_OWN) ? k : opp<L>(k);
-              if (k == 0 || !(nb & (1u << b))) PairStore<S>::st1(pl.dst[k] + cell + h, 0.0f);
-            }
-          }
-        }
-      }
-    } else {  // S_PUSH
-      const bool plain = fl0 && fl1 && !((w[0] | w[1]) & (kWordLinks | kWordMoving)) && !edge[0] && !edge[1];
-      if (plain) {
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) st_pair(pl.dst[i], n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
-      } else {
-        // per cell, with bounce-back links, domain edges and non-fluid cells
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t wd = w[h];
-          const int c = cell + h;
-          const float rh = h == 0 ? rho.v.x : rho.v.y;
-          Nbr c1;
-          c1.x = x0 + h;
-          c1.y = y;
-          c1.z = z;
-          if (wd & kWordFluid) {
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) {
-              const float fi = h == 0 ? f[i].v.x : f[i].v.y;
-              const int tx = 1 + h + L::c(i, 0);
-              const bool wall = i != 0 && (wd & (1u << i));
-              const bool out = i != 0 && edge[h] && outside(p, c1, L::c(i, 0), L::c(i, 1), L::c(i, 2));
-              if (wall || out) {
-                float bounced = fi;
-                float t;
-                if (wall && (wd & kWordMoving) &&
-                    moving_term<L>(p, n.at(tx, L::c(i, 1), L::c(i, 2)), i, wd, t))
-                  bounced -= rh * t;
-                PairStore<S>::st1(pl.dst[opp<L>(i)] + c, bounced);
-              } else {
-                PairStore<S>::st1(pl.dst[i] + n.at(tx, L::c(i, 1), L::c(i, 2)), fi);
-              }
-            }
-          } else if (OLB_SOLID_FILL) {
-            const uint32_t nb = wd & kWordLinks;
-#pragma unroll
-            for (int k = 0; k < L::Q; ++k)
-              if (k == 0 || !(nb & (1u << opp<L>(k)))) PairStore<S>::st1(pl.dst[k] + c, 0.0f);
-          }
-        }
-      }
-    }
-    if (STATS) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (w[h] & kWordFluid) {
-          const float dr = (h == 0 ? drho.v.x : drho.v.y) * INV_SCALE;
-          float jv[3], uv[3], v[8];
-#pragma unroll
-          for (int dd = 0; dd < 3; ++dd) {
-            jv[dd] = (h == 0 ? j[dd].v.x : j[dd].v.y) * INV_SCALE;
-            uv[dd] = h == 0 ? u[dd].v.x : u[dd].v.y;
-          }
-          stats_of(dr, jv, uv, v);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) sv[k] = (k == 5) ? fmaxf(sv[k], v[k]) : sv[k] + v[k];
-        }
-      }
-    }
+    pair_update<L, S, G, SC, STATS, WALLS, TRT>(p, pl, n, x0, y, z, w, gamma, f, sv);
   }
   if (STATS) block_reduce_row(sv, partials + 8 * block_linear(), false);
 }

@@ -58,6 +58,9 @@ SIGNATURES = {
     "olb_diagnostics": [_P, _P],
     "olb_adjoint_run": [_P, _I64, _I64, _P, _P, _P, _P],
     "olb_adjoint_run_misfit": [_P, _I64, _I64, _P, _P, _P, _P, _P],
+    "olb_set_force_field": [_P, _P],
+    "olb_inject_stalled_copy": [_P, _U, _I64],
+    "olb_adjoint_gradients": [_P, _I64, _I64, _P, _P, _P, _P],
     "olb_ade_create": [_I, _I, _I, _I, _I, _P],
     "olb_ade_destroy": [_P],
     "olb_ade_set_stream": [_P, _P],
@@ -83,6 +86,12 @@ class OlbError(RuntimeError):
 class Objective(ctypes.Structure):
     _fields_ = [("plane_axis", ctypes.c_int32), ("plane_index", ctypes.c_int32),
                 ("component", ctypes.c_int32)]
+
+
+class Gradients(ctypes.Structure):
+    """olb_gradients: output pointers of olb_adjoint_gradients (NULL = not computed)."""
+    _fields_ = [("loss", ctypes.c_void_p), ("dL_dgamma", ctypes.c_void_p), ("dL_dtau", ctypes.c_void_p),
+                ("dL_dF", ctypes.c_void_p)]
 
 
 _lib = None
@@ -253,6 +262,16 @@ class Lattice:
         FF = (ctypes.c_double * 3)(*[float(v) for v in (list(F) + [0, 0, 0])[:3]])
         _call("olb_set_force", self.handle, FF)
 
+    def set_force_field(self, F):
+        """Per-cell force density float64 [3, nz, ny, nx] (CUDA tensor or host array),
+        replacing the uniform force; None removes it."""
+        if F is None:
+            _call("olb_set_force_field", self.handle, None)
+            return
+        _check_array(F, "float64", 3 * self.cells, "F")
+        p, keep = _ptr(F)
+        _call("olb_set_force_field", self.handle, p)
+
     def set_porosity(self, gamma):
         if gamma is None:
             _call("olb_set_porosity", self.handle, None)
@@ -354,6 +373,46 @@ class Lattice:
         _call("olb_adjoint_run_misfit", self.handle, int(n_steps), int(checkpoint_every), pu, pr,
               ctypes.byref(loss), pg, ctypes.byref(dtau))
         return loss.value, dgamma, dtau.value
+
+    def adjoint_gradients(self, n_steps: int, checkpoint_every: int, objective=None, u_target=None, region=None,
+                          want=("dgamma", "dtau", "dforce")):
+        """Checkpointed adjoint of the plane objective (``objective`` = (axis, index,
+        component)) or of the velocity misfit (``u_target``, ``region``) with the
+        outputs named in ``want``: a dict with "loss" and any of "dgamma" (CUDA float64
+        [nz, ny, nx]), "dtau" (float), "dforce" (CUDA float64 [3, nz, ny, nx])."""
+        import torch
+
+        if (objective is None) == (u_target is None):
+            raise ValueError("give either objective or u_target")
+        loss, dtau = ctypes.c_double(), ctypes.c_double()
+        dg = torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device="cuda") \
+            if "dgamma" in want else None
+        dF = torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device="cuda") \
+            if "dforce" in want else None
+        out = Gradients(ctypes.addressof(loss), None if dg is None else dg.data_ptr(),
+                        ctypes.addressof(dtau) if "dtau" in want else None,
+                        None if dF is None else dF.data_ptr())
+        obj = None if objective is None else Objective(*[int(v) for v in objective])
+        pu = pr = None
+        keep = []
+        if u_target is not None:
+            _check_array(u_target, "float64", 3 * self.cells, "u_target")
+            pu, k = _ptr(u_target)
+            keep.append(k)
+        if region is not None:
+            _check_array(region, "uint8", self.cells, "region")
+            pr, k = _ptr(region)
+            keep.append(k)
+        _call("olb_adjoint_gradients", self.handle, int(n_steps), int(checkpoint_every),
+              None if obj is None else ctypes.byref(obj), pu, pr, ctypes.byref(out))
+        res = {"loss": loss.value}
+        if dg is not None:
+            res["dgamma"] = dg
+        if "dtau" in want:
+            res["dtau"] = dtau.value
+        if dF is not None:
+            res["dforce"] = dF
+        return res
 
     def synchronize(self):
         _call("olb_synchronize", self.handle)
@@ -489,3 +548,31 @@ def velocity_misfit_loss(lattice: Lattice, gamma, tau, f0, n_steps: int, checkpo
             return grad * dg.view_as(gamma), grad_tau
 
     return _VelocityMisfit.apply(gamma, tau)
+
+
+def force_misfit_loss(lattice: Lattice, force, f0, n_steps: int, checkpoint_every: int, u_target,
+                      region=None):
+    """J = 1/2 sum over the fluid cells of ``region`` of |u - u*|^2 after ``n_steps``
+    steps from ``f0`` as a differentiable function of the per-cell force density
+    ``force`` (float64 CUDA tensor [3, nz, ny, nx]): the objective and the control of
+    the guide's force-field identification (testFlowOpti3d, adjoint variant).  The
+    lattice's collision, tau and porosity stay as set; backward returns dJ/dF of
+    ``olb_adjoint_gradients``."""
+    import torch
+
+    class _ForceMisfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, F):
+            lattice.set_force_field(F.detach().contiguous())
+            lattice.set_populations(f0)
+            r = lattice.adjoint_gradients(n_steps, checkpoint_every, u_target=u_target, region=region,
+                                          want=("dforce",))
+            ctx.save_for_backward(r["dforce"])
+            return torch.tensor(r["loss"], dtype=torch.float64, device=F.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            (dF,) = ctx.saved_tensors
+            return grad * dF.view_as(force)
+
+    return _ForceMisfit.apply(force)

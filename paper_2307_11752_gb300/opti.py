@@ -1,5 +1,6 @@
 """Adjoint-driven optimisation of the porosity field (the guide's chapter
-"Optimization" and its example domainIdentification3d).
+"Optimization" and its example domainIdentification3d) and of the force field
+(example testFlowOpti3d, adjoint variant: three control components per cell).
 
 A control alpha lives on the cells of a design domain; the porosity there is
 gamma = p(alpha) for a projection p onto [0, 1] (section "Optimizer Classes",
@@ -110,4 +111,61 @@ def identify_porosity(evaluate: Callable, gamma_fixed, design, gamma_start, proj
     closure()  # J at the final control
     with torch.no_grad():
         res.gamma = compose(alpha)
+    return res
+
+
+def identify_force(evaluate: Callable, force_fixed, design, force_start=0.0, iterations: int = 20,
+                   history_size: int = 10, tolerance: float = 0.0, line_search_evaluations: int = 25) -> Result:
+    """Minimise J(F) over the force density of the design cells: the control is the
+    distributed field, three components at each design cell (testFlowOpti3d with the
+    adjoint LBM).  No projection: the force is unconstrained.
+
+    evaluate     F (float64 tensor [3, nz, ny, nx]) -> 0-d tensor J, differentiable in F
+                 (on the GPU: :func:`paper_2307_11752_gb300.olb.force_misfit_loss`)
+    force_fixed  force density outside the design domain ([3, nz, ny, nx])
+    design       bool tensor [nz, ny, nx]
+    force_start  initial force of the design cells (float, or tensor broadcastable
+                 to [3, n_design])
+    Returns a Result whose ``alpha`` is the control [3, n_design] and whose ``gamma``
+    field holds the identified force density [3, nz, ny, nx]."""
+    import torch
+
+    design = design.to(device=force_fixed.device, dtype=torch.bool)
+    nd = int(design.sum())
+    if nd == 0:
+        raise ValueError("the design domain holds no cell")
+    start = torch.as_tensor(force_start, dtype=torch.float64, device=force_fixed.device)
+    control = start.expand(3, nd).clone().detach().requires_grad_(True)
+    res = Result(alpha=control, gamma=None)
+
+    def compose(c):
+        F = force_fixed.clone()
+        F[:, design] = c
+        return F
+
+    opt = torch.optim.LBFGS([control], lr=1.0, max_iter=1, max_eval=line_search_evaluations,
+                            history_size=history_size, line_search_fn="strong_wolfe", tolerance_grad=0.0,
+                            tolerance_change=0.0)
+    record = [False]
+
+    def closure():
+        opt.zero_grad()
+        J = evaluate(compose(control))
+        J.backward()
+        res.evaluations += 1
+        if record[0]:
+            res.objective.append(float(J.detach()))
+            res.gradient_norm.append(float(control.grad.norm()))
+            record[0] = False
+        return J
+
+    for _ in range(iterations):
+        record[0] = True
+        opt.step(closure)
+        if res.objective[-1] <= tolerance:
+            break
+    record[0] = True
+    closure()
+    with torch.no_grad():
+        res.gamma = compose(control)
     return res

@@ -116,3 +116,16 @@ def porous_channel_case(nx=40, ny=14, nz=11, tau=0.8, seed=2, d=1, moving=False)
     F = (I.channel_force(ny, tau, 0.05), 0.0, 0.0)
     return Case(d, m, 1, tau, force=F, gamma=I.smoothed_porosity(seed, m), walls=walls,
                 noise=I.population_noise(seed + 1, q, m, 1e-4))
+
+
+def assert_cells_close(got, ref, rtol: float, floor: float):
+    """Per-cell bound |got - ref| <= rtol |ref| + floor max|ref| at every cell (no
+    norm over the field, so one badly wrong cell fails).  The floor only matters at
+    cells whose own gradient is below floor/rtol of the largest one."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    bound = rtol * np.abs(ref) + floor * np.max(np.abs(ref))
+    excess = np.abs(got - ref) - bound
+    k = int(np.argmax(excess))
+    assert excess.flat[k] <= 0, (f"cell {k}: got {got.flat[k]!r}, reference {ref.flat[k]!r}, "
+                                 f"bound {bound.flat[k]:.3e}")

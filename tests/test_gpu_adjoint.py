@@ -6,7 +6,7 @@ import pytest
 
 from paper_2307_11752_gb300 import inputs as I
 
-from _cases import porous_channel_case
+from _cases import assert_cells_close, porous_channel_case
 
 pytestmark = pytest.mark.gpu
 
@@ -47,8 +47,12 @@ def test_adjoint_f64_matches_oracle(oracle, olb, d, moving, K):
 
 
 @pytest.mark.parametrize("scheme", ["pull", "aa"])
-def test_adjoint_f32_storage_within_1e4(oracle, olb, scheme):
-    case = porous_channel_case(nx=30, ny=12, nz=10)
+@pytest.mark.parametrize("moving", [False, True])
+def test_adjoint_f32_storage_within_1e4(oracle, olb, scheme, moving):
+    """Per cell: |dL/dgamma - oracle| <= 1e-4 |oracle| + 1e-6 max|oracle| (the floor
+    covers the few cells whose gradient is ~1e-5 of the largest, next to a moving
+    wall)."""
+    case = porous_channel_case(nx=30, ny=12, nz=10, moving=moving)
     steps = 40
     obj = (0, case.shape[2] - 1, 0)
     lo, go, to = _oracle_adjoint(oracle, case, steps, obj)
@@ -57,7 +61,7 @@ def test_adjoint_f32_storage_within_1e4(oracle, olb, scheme):
     lg, gg, tg = g.adjoint_run(steps, 9, obj)
     gg = gg.cpu().numpy()
     assert abs(lg - lo) <= 1e-5 * abs(lo)
-    assert np.linalg.norm(gg - go) <= 1e-4 * np.linalg.norm(go)
+    assert_cells_close(gg, go, 1e-4, 1e-6)
     assert abs(tg - to) <= 2e-5 * abs(to)
     g.close()
 

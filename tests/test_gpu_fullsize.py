@@ -152,10 +152,15 @@ def test_channel_384_block_continuation_f16(oracle, olb):
     assert err <= 2e-3, err
 
 
-@pytest.mark.parametrize("dtype,tol,tol_tau", [("f64", 1e-6, 1e-6), ("f32", 1e-3, 1e-4)])
-def test_adjoint_channel256_matches_fp64_differences(olb, dtype, tol, tol_tau):
-    """Adjoint gradients on the 256 x 128 x 128 porous channel (100 steps, K = 25)
-    against central differences of FP64 GPU forward runs at 3 seeded cells + tau."""
+def test_adjoint_channel256_per_cell_against_differences(olb):
+    """FP32- and FP64-storage adjoints on the 256 x 128 x 128 porous channel (300
+    steps, K = 50) against central differences of FP64 GPU forward runs at 8 seeded
+    fluid cells and tau, per cell and with no absolute slack: FP64 within 1e-6, FP32
+    within 1e-4 relative.  The gradients are 1e-13 .. 1e-11 against a loss of ~4e-6,
+    so the step is h = 1e-3 (at 1e-5 the two losses share all but their last few
+    digits), and the quotients at h and h/2 are combined by Richardson extrapolation,
+    (4 D(h/2) - D(h)) / 3, which removes their h^2 truncation term (about 1e-6
+    relative at h = 1e-3)."""
     import torch
 
     nx, ny, nz = 256, 128, 128
@@ -163,7 +168,7 @@ def test_adjoint_channel256_matches_fp64_differences(olb, dtype, tol, tol_tau):
     gamma = I.smoothed_porosity(2, m)
     tau = 0.8
     F = (I.channel_force(ny, tau), 0.0, 0.0)
-    steps, K = 100, 25
+    steps, K = 300, 50
     obj = (0, nx - 1, 0)
 
     def lattice(dt):
@@ -172,36 +177,47 @@ def test_adjoint_channel256_matches_fp64_differences(olb, dtype, tol, tol_tau):
         lat.set_force(F)
         return lat
 
-    lat = lattice(dtype)
-    lat.set_bgk(tau)
-    lat.set_porosity(torch.from_numpy(gamma.reshape(-1).copy()).cuda())
-    lat.init_equilibrium()
-    loss, dg, dtau = lat.adjoint_run(steps, K, obj)
-    dg = dg.cpu().numpy().reshape(-1)
-    lat.close()
+    grads = {}
+    for dt in ("f32", "f64"):
+        lat = lattice(dt)
+        lat.set_bgk(tau)
+        lat.set_porosity(torch.from_numpy(gamma.reshape(-1).copy()).cuda())
+        lat.init_equilibrium()
+        loss, dg, dtau = lat.adjoint_run(steps, K, obj)
+        grads[dt] = (dg.cpu().numpy().reshape(-1), dtau)
+        lat.close()
+        del dg
+        torch.cuda.empty_cache()
     ref = lattice("f64")
+    plane = torch.from_numpy(m[:, :, nx - 1] == I.FLUID).cuda()
 
     def run(gam, t):
         ref.set_bgk(t)
         ref.set_porosity(torch.from_numpy(gam.reshape(-1).copy()).cuda())
         ref.init_equilibrium()
         ref.step(steps)
-        rho, u = ref.moments()
-        plane = u[0, :, :, nx - 1].cpu().numpy()
-        return float(plane[m[:, :, nx - 1] == I.FLUID].mean())
+        _, u = ref.moments()
+        return float(u[0, :, :, nx - 1][plane].mean())
 
-    h = 1e-5
-    # cells inside the domain of dependence of the outlet plane after 100 steps
-    near = m.copy()
-    near[:, :, 40:nx - 60] = 0
-    for c in I.random_fluid_cells(3, near, 3):
+    def quotient(c, h):
         gp = gamma.copy().reshape(-1)
         gm = gp.copy()
         gp[c] += h
         gm[c] -= h
-        fd = (run(gp, tau) - run(gm, tau)) / (2 * h)
-        assert abs(fd - dg[c]) <= tol * abs(fd) + 1e-11, (c, fd, dg[c])
+        return (run(gp, tau) - run(gm, tau)) / (2 * h)
+
+    h = 1e-3
+    # cells the outlet plane's adjoint reaches within 300 steps (elsewhere the
+    # gradient is below 1e-25 and a difference quotient of FP64 runs gives 0)
+    near = m.copy()
+    near[:, :, 40:nx - 60] = 0
+    cells = I.random_fluid_cells(3, near, 8)
+    fd = [(4 * quotient(c, h / 2) - quotient(c, h)) / 3 for c in cells]
+    for c, d in zip(cells, fd):
+        assert abs(grads["f64"][0][c] - d) <= 1e-6 * abs(d), (c, d, grads["f64"][0][c])
+        assert abs(grads["f32"][0][c] - d) <= 1e-4 * abs(d), (c, d, grads["f32"][0][c])
     ht = 1e-6
-    fd = (run(gamma, tau + ht) - run(gamma, tau - ht)) / (2 * ht)
-    assert abs(fd - dtau) <= tol_tau * abs(fd), (fd, dtau)
+    d = (run(gamma, tau + ht) - run(gamma, tau - ht)) / (2 * ht)
+    assert abs(grads["f64"][1] - d) <= 1e-6 * abs(d)
+    assert abs(grads["f32"][1] - d) <= 1e-4 * abs(d)
     ref.close()

@@ -7,7 +7,7 @@ import pytest
 
 from paper_2307_11752_gb300 import inputs as I
 
-from _cases import porous_channel_case
+from _cases import assert_cells_close, porous_channel_case
 
 pytestmark = pytest.mark.gpu
 
@@ -93,9 +93,9 @@ def test_misfit_adjoint_reduced_storage(oracle, olb, dtype):
     g = case.gpu(dtype, "pull")
     lg, gg, tg = g.adjoint_run_misfit(steps, 9, u_t, region)
     gg = gg.cpu().numpy()
-    tol = 1e-4 if dtype == "f32" else 2e-2
+    tol, floor = (1e-4, 1e-6) if dtype == "f32" else (2e-2, 5e-4)
     assert abs(lg - lo) <= tol * abs(lo)
-    assert np.linalg.norm(gg - go) <= tol * np.linalg.norm(go)
+    assert_cells_close(gg, go, tol, floor)
     assert abs(tg - to) <= tol * abs(to)
     g.close()
 

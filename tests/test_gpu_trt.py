@@ -2,7 +2,8 @@
 populations within 1e-12 (FP64) and 1e-5 (FP32) relative, both streaming patterns,
 the one-cell-per-thread kernel (odd nx) and the paired kernel (even nx), moving
 walls, Guo force and porosity; FP16 within its storage bound; the exact Poiseuille
-parabola at Lambda = 3/16; the adjoint refuses TRT."""
+parabola at Lambda = 3/16; the adjoint of the TRT map against the oracle's TRT
+adjoint (FP64 to 1e-10), against central differences, and with reduced storage."""
 import dataclasses
 
 import numpy as np
@@ -10,7 +11,7 @@ import pytest
 
 from paper_2307_11752_gb300 import inputs as I
 
-from _cases import Case, cavity_case, porous_channel_case, rel_err
+from _cases import Case, assert_cells_close, cavity_case, porous_channel_case, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -98,17 +99,122 @@ def test_trt_poiseuille_exact_on_the_gpu(olb, tau):
     lat.close()
 
 
-def test_adjoint_refuses_trt_and_bgk_restores(olb):
-    case = dataclasses.replace(porous_channel_case(nx=12, ny=8, nz=6), collision="trt")
+@pytest.mark.parametrize("d,moving", [(1, False), (0, True), (1, True)])
+@pytest.mark.parametrize("magic", [3.0 / 16.0, 1.0 / 12.0])
+def test_trt_adjoint_f64_matches_oracle(oracle, olb, d, moving, magic):
+    """The GPU adjoint of the TRT map (moment form) against the oracle's explicit TRT
+    Jacobian: loss, dL/dgamma and dL/dtau at fixed magic parameter."""
+    case = dataclasses.replace(porous_channel_case(nx=22, ny=10, nz=8, d=d, moving=moving),
+                               collision="trt", magic=magic)
+    steps, K = 23, 7
+    obj = (0, case.shape[2] - 1, 0)
+    lat = case.oracle(oracle)
+    lo, go, to = lat.adjoint(case.oracle_state(lat), steps, obj)
     g = case.gpu("f64", "pull")
-    with pytest.raises(olb.OlbError) as e:
-        g.adjoint_run(3, 2, (0, 11, 0))
-    assert e.value.status == -7
-    with pytest.raises(olb.OlbError) as e:
-        g.adjoint_run_misfit(3, 2, np.zeros((3,) + case.shape), None)
-    assert e.value.status == -7
-    with pytest.raises(olb.OlbError):
-        g.set_trt(0.8, 0.0)
-    g.set_bgk(case.tau)
-    g.adjoint_run(3, 2, (0, 11, 0))
+    lg, gg, tg = g.adjoint_run(steps, K, obj)
+    gg = gg.cpu().numpy()
     g.close()
+    assert abs(lg - lo) <= 1e-13 * abs(lo)
+    assert np.max(np.abs(gg - go)) <= 1e-10 * np.max(np.abs(go))
+    assert abs(tg - to) <= 1e-10 * abs(to)
+
+
+def test_trt_adjoint_misfit_f64_matches_oracle(oracle, olb):
+    case = dataclasses.replace(porous_channel_case(nx=20, ny=10, nz=8, moving=True), collision="trt",
+                               magic=3.0 / 16.0)
+    steps = 19
+    target = 0.01 * (I.uniform(31, (3,) + case.shape) - 0.5)
+    region = (I.uniform(32, case.shape) < 0.5).astype(np.uint8)
+    lat = case.oracle(oracle)
+    lo, go, to = lat.adjoint(case.oracle_state(lat), steps, oracle.Misfit(target, region))
+    g = case.gpu("f64", "pull")
+    lg, gg, tg = g.adjoint_run_misfit(steps, 5, target, region)
+    gg = gg.cpu().numpy()
+    g.close()
+    assert abs(lg - lo) <= 1e-12 * abs(lo)
+    assert np.max(np.abs(gg - go)) <= 1e-10 * np.max(np.abs(go))
+    assert abs(tg - to) <= 1e-10 * abs(to)
+
+
+def test_trt_adjoint_matches_gpu_central_differences(olb):
+    """dL/dgamma and dL/dtau (magic parameter fixed) of the TRT map against central
+    differences of FP64 forward runs on the GPU."""
+    import torch
+
+    case = dataclasses.replace(porous_channel_case(nx=24, ny=11, nz=9), collision="trt", magic=3.0 / 16.0)
+    steps = 30
+    obj = (0, case.shape[2] - 1, 0)
+    g = case.gpu("f64", "pull")
+    f0 = g.get_populations().clone()
+    loss, dg, dtau = g.adjoint_run(steps, 8, obj)
+    dg = dg.cpu().numpy().reshape(-1)
+
+    def run(gamma=None, tau=None):
+        g.set_porosity(torch.from_numpy((gamma if gamma is not None else case.gamma).reshape(-1).copy()).cuda())
+        g.set_trt(tau if tau is not None else case.tau, case.magic)
+        g.set_populations(f0)
+        g.step(steps)
+        _, u = g.moments()
+        plane = torch.from_numpy(case.material[:, :, -1] == I.FLUID).cuda()
+        return float(u[0, :, :, -1][plane].mean())
+
+    h = 1e-5
+    for c in I.random_fluid_cells(4, case.material, 8):
+        gp = case.gamma.copy().reshape(-1)
+        gm = gp.copy()
+        gp[c] += h
+        gm[c] -= h
+        fd = (run(gamma=gp.reshape(case.shape)) - run(gamma=gm.reshape(case.shape))) / (2 * h)
+        assert abs(fd - dg[c]) <= 1e-4 * abs(fd) + 1e-15
+    ht = 1e-6
+    fd = (run(tau=case.tau + ht) - run(tau=case.tau - ht)) / (2 * ht)
+    assert abs(fd - dtau) <= 1e-4 * abs(fd)
+    g.close()
+
+
+@pytest.mark.parametrize("dtype,scheme", [("f32", "pull"), ("f32", "aa"), ("f16", "pull")])
+def test_trt_adjoint_reduced_storage(oracle, olb, dtype, scheme):
+    case = dataclasses.replace(porous_channel_case(nx=30, ny=12, nz=10, moving=True), collision="trt",
+                               magic=3.0 / 16.0)
+    steps = 40
+    obj = (0, case.shape[2] - 1, 0)
+    lat = case.oracle(oracle)
+    lo, go, to = lat.adjoint(case.oracle_state(lat), steps, obj)
+    g = case.gpu(dtype, scheme)
+    lg, gg, tg = g.adjoint_run(steps, 9, obj)
+    gg = gg.cpu().numpy()
+    g.close()
+    tol, floor = {"f32": (1e-4, 1e-6), "f16": (2e-2, 5e-4)}[dtype]
+    assert abs(lg - lo) <= tol * abs(lo)
+    assert_cells_close(gg, go, tol, floor)
+    assert abs(tg - to) <= tol * abs(to)
+
+
+def test_switching_collision_between_adjoint_runs(olb):
+    """BGK and TRT runs on one handle: each adjoint follows the collision selected
+    when it starts, and TRT at Lambda = (tau - 1/2)^2 gives the BGK loss and
+    dL/dgamma (not dL/dtau: TRT's holds Lambda fixed while BGK's moves it with tau)."""
+    case = porous_channel_case(nx=16, ny=8, nz=6)
+    g = case.gpu("f64", "pull")
+    f0 = g.get_populations().clone()
+    obj = (0, 15, 0)
+    g.set_populations(f0)  # every run starts from the same stored state
+    lb, gb, tb = g.adjoint_run(9, 4, obj)
+    g.set_trt(case.tau, (case.tau - 0.5) ** 2)
+    g.set_populations(f0)
+    lt, gt, tt = g.adjoint_run(9, 4, obj)
+    g.set_bgk(case.tau)
+    g.set_populations(f0)
+    lb2, gb2, tb2 = g.adjoint_run(9, 4, obj)
+    g.close()
+    gb, gt, gb2 = (x.cpu().numpy() for x in (gb, gt, gb2))
+    assert lb2 == lb and np.array_equal(gb2, gb) and tb2 == tb
+    assert abs(lt - lb) <= 1e-14 * abs(lb)
+    assert np.max(np.abs(gt - gb)) <= 1e-11 * np.max(np.abs(gb))
+    assert np.isfinite(tt) and tt != tb
+    with pytest.raises(olb.OlbError):
+        g2 = case.gpu("f64", "pull")
+        try:
+            g2.set_trt(0.8, 0.0)
+        finally:
+            g2.close()
