@@ -279,6 +279,39 @@ int olb_adjoint_gradients(olb_handle h, int64_t n_steps, int64_t checkpoint_ever
  * reports asynchronous CUDA errors as OLB_ERR_CUDA. */
 int olb_synchronize(olb_handle h);
 
+/* ---------------------------------------------------------------------------
+ * Slab decomposition along z (the guide's parallel block decomposition with its
+ * communicator, section "Communication": each block exchanges one layer of
+ * populations with its neighbours per step).  A slab is an ordinary D3Q19 lattice
+ * holding its share of the planes plus one halo plane on each z face: its material
+ * carries the neighbouring slabs' planes there (void where the global lattice ends
+ * on a non-periodic z face), and z is not periodic in it.  After each pull step the
+ * populations leaving each interior face are packed, carried to the neighbouring
+ * slab by any transport (a device copy between slabs on one GPU), and unpacked into
+ * its halo plane; the next step then reads exactly what the single lattice would.
+ * Only the pull scheme is supported.
+ * --------------------------------------------------------------------------- */
+
+/* Planes z_first .. z_last are updated by the steps and counted by olb_diagnostics;
+ * the planes outside are halo planes.  (-1, -1) makes every plane active again.
+ * Errors: OLB_ERR_ARG (empty or out-of-range). */
+int olb_set_active_planes(olb_handle h, int z_first, int z_last);
+
+/* Values per face buffer (populations crossing a z face times nx * ny) and the bytes
+ * per value (the storage type's: buffers hold stored values unconverted). */
+int olb_halo_size(olb_handle h, int64_t* values, int* elem_bytes);
+
+/* Pack the populations that leave the active planes through face 0 (low z: those
+ * with c_z = -1 at plane z_first) or face 1 (high z: c_z = +1 at plane z_last) into
+ * buf, [population][y][x].  Unpack buf, packed by the neighbour across that face,
+ * into the halo plane of face 0 (z_first - 1) or 1 (z_last + 1); only cells that
+ * are fluid there receive values (a wall cell's slots hold its fluid neighbours'
+ * bounce-back values).  buf is device memory of olb_halo_size values; queued on
+ * the handle's stream.  Errors: OLB_ERR_STATE (no halo planes set, state not the one
+ * after a pull step), OLB_ERR_UNSUPPORTED (not D3Q19), OLB_ERR_ARG. */
+int olb_halo_pack(olb_handle h, int face, void* buf);
+int olb_halo_unpack(olb_handle h, int face, const void* buf);
+
 /* Failure injection for tests of the device-side timeout path (not for production
  * use; the guide has no counterpart).  The next step of the handle that runs the
  * TMA-fed pull kernel (FP32 or 16-bit storage, even nx, no force field; the state
@@ -331,7 +364,8 @@ int olb_statistics_noalloc(olb_descriptor d, int nx, int ny, int nz, const doubl
  * diffusivity mu = cs2 (tau - 1/2); D2Q5: w = 1/3 (rest), 1/6, cs2 = 1/3; D3Q7:
  * w = 1/4, 1/8, cs2 = 1/4 (the guide names these descriptors without printing
  * their tables; the tables follow from sum w = 1 and sum w c_a c_b = cs2 delta).
- * Every axis is periodic.  The velocity v is prescribed (uniform or per cell).
+ * Every axis is periodic unless olb_ade_set_material sets walls.  The velocity v is
+ * prescribed (uniform or per cell) or taken from a fluid lattice.
  * The handle keeps the canonical state g(t) in two buffers of q x cells values
  * (F64 or F32), obtained through the olb_set_allocator provider.  Calls queue
  * work on the handle's stream (olb_ade_set_stream, default stream 0).
@@ -349,6 +383,26 @@ int olb_ade_set_tau(olb_ade_handle h, double tau);
  * (host or device, copied during the call; takes precedence when both are given).
  * The z component is ignored on D2Q5.  Errors: OLB_ERR_ARG (both NULL, non-finite). */
 int olb_ade_set_velocity(olb_ade_handle h, const double v[3], const double* v_field);
+/* Boundaries of the advection-diffusion lattice: material uint8 [cells] (host or
+ * device) with 1 = bulk cell, 0 = no-flux wall (a link into it bounces back,
+ * g_opp(i)(x) = g*_i(x)), 2..255 = Dirichlet cell of value wall_C[m] (the guide's
+ * constant-temperature boundary, named without its scheme, read as anti-bounce-
+ * back: g_opp(i)(x) = -g*_i(x) + 2 w_i C_w, which holds C_w at the link's midpoint);
+ * periodic_mask: the axes that wrap (links leaving the domain along the others
+ * bounce back like a no-flux wall); wall_C: double[256] on the host, or NULL when no
+ * cell is Dirichlet.  Non-bulk cells keep their values.  Without this call every
+ * cell is bulk and every axis periodic.
+ * Errors: OLB_ERR_ARG (null material, bad mask, Dirichlet cells without wall_C,
+ *         non-finite wall values). */
+int olb_ade_set_material(olb_ade_handle h, const uint8_t* material, unsigned periodic_mask, const double* wall_C);
+
+/* Advection velocity from a fluid lattice of the same size (D2Q9 for D2Q5, D3Q19
+ * for D3Q7): v = u = (j + F/2)/rho of its current state, computed on the device
+ * into this handle's velocity field (ordered after the fluid's queued work), so a
+ * coupled step is olb_step(fluid, 1); olb_ade_set_velocity_from(h, fluid);
+ * olb_ade_step(h, 1).  Errors: OLB_ERR_ARG (size or dimension mismatch). */
+int olb_ade_set_velocity_from(olb_ade_handle h, olb_handle fluid);
+
 /* g = g^eq(C, v) from C double [cells] (host or device). */
 int olb_ade_init(olb_ade_handle h, const double* C);
 /* n collide-and-stream steps. */

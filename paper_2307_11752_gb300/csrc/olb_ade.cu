@@ -11,6 +11,15 @@
 // (pre-collision) state: the thread loads its own q values (coalesced), collides
 // and stores each post-collision value at x + c_i of the other buffer (coalesced up
 // to a one-element shift).  7 x 2 stored values per cell update.
+//
+// Boundaries (section "Advection--Diffusion Equation" names a constant-temperature
+// boundary without its scheme; read as anti-bounce-back, the oracle's reading): a
+// link of a bulk cell x that hits a no-flux wall cell, or leaves the domain along a
+// non-periodic axis, bounces back, g_opp(i)(x) = g*_i(x); one that hits a Dirichlet
+// cell of value C_w reflects with the opposite sign, g_opp(i)(x) = -g*_i(x) + 2 w_i C_w,
+// which holds C_w at the link's midpoint.  Non-bulk cells keep their values.  A
+// host-made mask per cell marks the links that need this, so bulk cells away from
+// walls take no extra load beyond the mask.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -47,6 +56,10 @@ struct AdeParams {
   T omega;
   T vu[3];
   const double* __restrict__ vf;  // [3][n] or nullptr (uniform vu)
+  const uint8_t* __restrict__ mat;
+  const uint8_t* __restrict__ lmask;
+  const double* __restrict__ wall_C;
+  unsigned periodic;
 };
 
 template <class T>
@@ -59,6 +72,10 @@ AdeParams<T> to_params(const AdeHost& h) {
   p.omega = (T)h.omega;
   for (int a = 0; a < 3; ++a) p.vu[a] = (T)h.vu[a];
   p.vf = h.vf;
+  p.mat = h.mat;
+  p.lmask = h.lmask;
+  p.wall_C = h.wall_C;
+  p.periodic = h.mat ? h.periodic : 7u;
   return p;
 }
 
@@ -98,6 +115,12 @@ __global__ void __launch_bounds__(256) k_ade_step(AdeParams<T> p, const T* __res
     g[i] = src[i * p.n + c];
     C += g[i];
   }
+  const unsigned links = p.lmask ? p.lmask[c] : 0u;
+  if (p.mat && p.mat[c] != 1) {  // non-bulk cells keep their values
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) dst[i * p.n + c] = g[i];
+    return;
+  }
   T v[3], geq[L::Q];
   velocity(p, c, v);
   equilibrium<L>(C, v, geq);
@@ -108,7 +131,25 @@ __global__ void __launch_bounds__(256) k_ade_step(AdeParams<T> p, const T* __res
   for (int i = 0; i < L::Q; ++i) {
     const T gs = g[i] - p.omega * (g[i] - geq[i]);
     const int64_t t = ((int64_t)zs[1 + L::c(i, 2)] * p.ny + ys[1 + L::c(i, 1)]) * p.nx + xs[1 + L::c(i, 0)];
-    dst[i * p.n + t] = gs;
+    if (!(links & (1u << i))) {
+      dst[i * p.n + t] = gs;
+      continue;
+    }
+    // wall link: the target is a non-bulk cell, or outside the domain (the wrapped
+    // index then names a cell on the far side, but the link leaves along a
+    // non-periodic axis exactly when the unwrapped coordinate is out of range)
+    const int q[3] = {x + L::c(i, 0), y + L::c(i, 1), z + L::c(i, 2)};
+    const int e[3] = {p.nx, p.ny, p.nz};
+    bool leaves = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if ((q[a] < 0 || q[a] >= e[a]) && !(p.periodic & (1u << a))) leaves = true;
+    const int m = leaves ? 0 : p.mat[t];
+    const int o = i == 0 ? 0 : (i <= L::Q / 2 ? i + L::Q / 2 : i - L::Q / 2);
+    if (m >= 2)
+      dst[o * p.n + c] = -gs + T(2) * (T)L::w(i) * (T)p.wall_C[m];
+    else
+      dst[o * p.n + c] = gs;
   }
 }
 

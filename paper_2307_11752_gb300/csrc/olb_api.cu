@@ -331,6 +331,7 @@ struct olb_lattice {
   double magic = 0.25;
   bool has_gamma = false;
   bool has_ffield = false;  // a per-cell force density replaces the uniform force
+  int za = 0, zb = 1 << 30;  // active planes (olb_set_active_planes); the others are halo planes
   unsigned inject_tx = 0;   // failure injection for the next step (olb_inject_stalled_copy)
   int64_t inject_ns = 0;
   int64_t time = 0, launches = 0;
@@ -367,8 +368,11 @@ struct olb_lattice {
     p.outside_links = outside_links ? 1 : 0;
     p.y0 = y0;
     p.y1 = y1;
-    p.z0 = z0;
-    p.z1 = z1;
+    p.z0 = std::max(z0, za);
+    p.z1 = std::min(z1, zb);
+    p.az0 = za;
+    p.az1 = std::min(zb, nz - 1);
+    if (p.z1 < p.z0) p.z0 = p.z1 = std::max(0, std::min(za, nz - 1));  // no fluid in the active planes
     p.err = static_cast<unsigned*>(err.p);
     p.inject_extra_tx = inject_tx;
     p.inject_wait_ns = (unsigned long long)inject_ns;
@@ -1155,6 +1159,134 @@ int olb_synchronize(olb_handle h) {
   return check_error_word(h);
 }
 
+}  // extern "C"
+
+namespace olb {
+// Slots of the populations that cross a z face of a slab, and the kernels that move
+// one plane's worth of them between a lattice and a caller's buffer.
+struct HaloSlots {
+  int n;
+  int s[8];
+};
+
+template <class E>
+__global__ void k_halo_pack(const E* __restrict__ state, int64_t pitch, HaloSlots sl, int64_t plane_cells,
+                            int64_t plane_offset, E* __restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= plane_cells) return;
+#pragma unroll 1
+  for (int k = 0; k < sl.n; ++k) out[k * plane_cells + c] = state[sl.s[k] * pitch + plane_offset + c];
+}
+
+// Only cells that are fluid receive: a wall cell of the halo plane holds in these
+// slots the bounce-back values its own fluid neighbours stored there.
+template <class E>
+__global__ void k_halo_unpack(E* __restrict__ state, int64_t pitch, HaloSlots sl, int64_t plane_cells,
+                              int64_t plane_offset, const uint8_t* __restrict__ mat, const E* __restrict__ in) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= plane_cells || mat[plane_offset + c] != 1) return;
+#pragma unroll 1
+  for (int k = 0; k < sl.n; ++k) state[sl.s[k] * pitch + plane_offset + c] = in[k * plane_cells + c];
+}
+}  // namespace olb
+
+namespace {
+
+// Populations with c_z == cz of the handle's lattice.
+HaloSlots halo_slots(olb_handle h, int cz) {
+  HaloSlots sl;
+  sl.n = 0;
+  for (int i = 0; i < h->q; ++i) {
+    const int c = h->desc == OLB_D2Q9 ? D2Q9::c(i, 2) : D3Q19::c(i, 2);
+    if (c == cz) sl.s[sl.n++] = i;
+  }
+  return sl;
+}
+
+// Checks shared by pack and unpack; plane index of the face.
+int halo_check(olb_handle h, int face, const void* buf, bool unpack, int* plane) {
+  if (h->desc != OLB_D3Q19) return fail(OLB_ERR_UNSUPPORTED, "slab halos are along z, on D3Q19");
+  if (face != 0 && face != 1) return fail(OLB_ERR_ARG, "face must be 0 (low z) or 1 (high z)");
+  if (!buf) return fail(OLB_ERR_ARG, "null halo buffer");
+  bool dev = false;
+  int rc = locate(buf, &dev, "halo buffer");
+  if (rc) return rc;
+  if (!dev) return fail(OLB_ERR_ARG, "the halo buffer must be device memory");
+  if (h->za < 1 || h->zb > h->nz - 2)
+    return fail(OLB_ERR_STATE, "set active planes that leave a halo plane on both z faces first");
+  if (h->scheme != OLB_PULL || h->repr != POST)
+    return fail(OLB_ERR_STATE, "halos are exchanged between pull steps (state after a step, pull scheme)");
+  *plane = unpack ? (face == 0 ? h->za - 1 : h->zb + 1) : (face == 0 ? h->za : h->zb);
+  return OLB_OK;
+}
+
+template <class E>
+int halo_launch(olb_handle h, bool unpack, HaloSlots sl, int plane, void* buf) {
+  const int64_t pc = (int64_t)h->nx * h->ny;
+  const int nb = (int)((pc + 255) / 256);
+  E* state = static_cast<E*>(h->buf[h->cur].p);
+  if (unpack)
+    k_halo_unpack<E><<<nb, 256, 0, h->stream>>>(state, h->pitch, sl, pc, plane * pc,
+                                                 static_cast<const uint8_t*>(h->mat.p), static_cast<const E*>(buf));
+  else
+    k_halo_pack<E><<<nb, 256, 0, h->stream>>>(state, h->pitch, sl, pc, plane * pc, static_cast<E*>(buf));
+  return launched(h, cudaGetLastError(), unpack ? "halo unpack" : "halo pack");
+}
+
+int halo_move(olb_handle h, int face, void* buf, bool unpack) {
+  int plane = 0;
+  int rc = halo_check(h, face, buf, unpack, &plane);
+  if (rc) return rc;
+  // the populations that leave through the face: c_z = -1 at the low face, +1 at the
+  // high face; a halo plane receives those that enter: +1 at the low, -1 at the high
+  const int cz = unpack ? (face == 0 ? 1 : -1) : (face == 0 ? -1 : 1);
+  const HaloSlots sl = halo_slots(h, cz);
+  switch (h->kt->state_elem) {
+    case 8: return halo_launch<uint64_t>(h, unpack, sl, plane, buf);
+    case 4: return halo_launch<uint32_t>(h, unpack, sl, plane, buf);
+    default: return halo_launch<uint16_t>(h, unpack, sl, plane, buf);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int olb_set_active_planes(olb_handle h, int z_first, int z_last) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (z_first == -1 && z_last == -1) {
+    h->za = 0;
+    h->zb = 1 << 30;
+    return OLB_OK;
+  }
+  if (z_first < 0 || z_last >= h->nz || z_first > z_last) return fail(OLB_ERR_ARG, "bad plane range");
+  h->za = z_first;
+  h->zb = z_last;
+  return OLB_OK;
+}
+
+int olb_halo_size(olb_handle h, int64_t* values, int* elem_bytes) {
+  int rc = check(h);
+  if (rc) return rc;
+  if (h->desc != OLB_D3Q19) return fail(OLB_ERR_UNSUPPORTED, "slab halos are along z, on D3Q19");
+  if (values) *values = (int64_t)halo_slots(h, 1).n * h->nx * h->ny;
+  if (elem_bytes) *elem_bytes = (int)h->kt->state_elem;
+  return OLB_OK;
+}
+
+int olb_halo_pack(olb_handle h, int face, void* buf) {
+  int rc = check(h);
+  if (rc) return rc;
+  return halo_move(h, face, buf, false);
+}
+
+int olb_halo_unpack(olb_handle h, int face, const void* buf) {
+  int rc = check(h);
+  if (rc) return rc;
+  return halo_move(h, face, const_cast<void*>(buf), true);
+}
+
 int olb_inject_stalled_copy(olb_handle h, unsigned extra_bytes, int64_t wait_ns) {
   int rc = check(h);
   if (rc) return rc;
@@ -1274,11 +1406,13 @@ struct olb_ade {
   int nx = 0, ny = 0, nz = 0;
   int64_t ncell = 0;
   cudaStream_t stream = nullptr;
-  DevBuf buf[2], vfield, stage;
+  DevBuf buf[2], vfield, stage, mat, lmask, wallC;
   int cur = 0;
   double tau = 1.0;
   double vu[3] = {0.0, 0.0, 0.0};
   bool has_vfield = false;
+  bool has_bc = false;     // olb_ade_set_material was called
+  unsigned periodic = 7u;
   size_t elem() const { return dtype == OLB_F64 ? sizeof(double) : sizeof(float); }
   size_t state_bytes() const { return (size_t)q * ncell * elem(); }
   AdeHost host() const {
@@ -1292,6 +1426,10 @@ struct olb_ade {
     a.omega = 1.0 / tau;
     for (int k = 0; k < 3; ++k) a.vu[k] = vu[k];
     a.vf = has_vfield ? static_cast<const double*>(vfield.p) : nullptr;
+    a.mat = has_bc ? static_cast<const uint8_t*>(mat.p) : nullptr;
+    a.lmask = has_bc ? static_cast<const uint8_t*>(lmask.p) : nullptr;
+    a.wall_C = has_bc ? static_cast<const double*>(wallC.p) : nullptr;
+    a.periodic = has_bc ? periodic : 7u;
     a.stream = stream;
     return a;
   }
@@ -1398,6 +1536,83 @@ int olb_ade_set_velocity(olb_ade_handle h, const double v[3], const double* v_fi
     for (int a = 0; a < 3; ++a) h->vu[a] = (h->q == 5 && a == 2) ? 0.0 : v[a];
     h->has_vfield = false;
   }
+  return OLB_OK;
+}
+
+int olb_ade_set_material(olb_ade_handle h, const uint8_t* material, unsigned periodic_mask, const double* wall_C) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  if (!material) return fail(OLB_ERR_ARG, "null material array");
+  if (periodic_mask > 7 || (h->q == 5 && (periodic_mask & 4u))) return fail(OLB_ERR_ARG, "bad periodic mask %u", periodic_mask);
+  const size_t n = (size_t)h->ncell;
+  std::vector<uint8_t> m(n), lm(n);
+  OLB_CUDA(cudaMemcpyAsync(m.data(), material, n, cudaMemcpyDefault, h->stream), "material read");
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "material sync");
+  double wc[256] = {0.0};
+  bool dirichlet = false;
+  for (size_t c = 0; c < n; ++c) dirichlet |= m[c] >= 2;
+  if (dirichlet && !wall_C) return fail(OLB_ERR_ARG, "Dirichlet cells (material >= 2) need wall_C");
+  if (wall_C) {
+    for (int k = 0; k < 256; ++k) {
+      wc[k] = wall_C[k];
+      if (!std::isfinite(wc[k])) return fail(OLB_ERR_ARG, "non-finite wall value");
+    }
+  }
+  // per bulk cell: bit i when x + c_i is not a bulk cell or lies outside a non-periodic face
+  static const int c5[5][3] = {{0, 0, 0}, {-1, 0, 0}, {0, -1, 0}, {1, 0, 0}, {0, 1, 0}};
+  static const int c7[7][3] = {{0, 0, 0}, {-1, 0, 0}, {0, -1, 0}, {0, 0, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  const int e[3] = {h->nx, h->ny, h->nz};
+  for (int z = 0; z < h->nz; ++z)
+    for (int y = 0; y < h->ny; ++y)
+      for (int x = 0; x < h->nx; ++x) {
+        const size_t c = ((size_t)z * h->ny + y) * h->nx + x;
+        unsigned bits = 0;
+        if (m[c] == 1) {
+          for (int i = 1; i < h->q; ++i) {
+            const int* ci = h->q == 5 ? c5[i] : c7[i];
+            int p[3] = {x + ci[0], y + ci[1], z + ci[2]};
+            bool inside = true;
+            for (int a = 0; a < 3; ++a)
+              if (p[a] < 0 || p[a] >= e[a]) {
+                if (periodic_mask & (1u << a)) p[a] = (p[a] + e[a]) % e[a];
+                else inside = false;
+              }
+            if (!inside || m[((size_t)p[2] * h->ny + p[1]) * h->nx + p[0]] != 1) bits |= 1u << i;
+          }
+        }
+        lm[c] = (uint8_t)bits;
+      }
+  if ((rc = h->mat.reserve(n)) || (rc = h->lmask.reserve(n)) || (rc = h->wallC.reserve(sizeof(wc)))) return rc;
+  OLB_CUDA(cudaMemcpyAsync(h->mat.p, m.data(), n, cudaMemcpyHostToDevice, h->stream), "material upload");
+  OLB_CUDA(cudaMemcpyAsync(h->lmask.p, lm.data(), n, cudaMemcpyHostToDevice, h->stream), "mask upload");
+  OLB_CUDA(cudaMemcpyAsync(h->wallC.p, wc, sizeof(wc), cudaMemcpyHostToDevice, h->stream), "wall upload");
+  OLB_CUDA(cudaStreamSynchronize(h->stream), "material sync");
+  h->periodic = periodic_mask;
+  h->has_bc = true;
+  return OLB_OK;
+}
+
+int olb_ade_set_velocity_from(olb_ade_handle h, olb_handle fluid) {
+  int rc = ade_check(h);
+  if (rc) return rc;
+  if ((rc = check(fluid))) return rc;
+  if (fluid->nx != h->nx || fluid->ny != h->ny || fluid->nz != h->nz || fluid->dim != (h->q == 5 ? 2 : 3))
+    return fail(OLB_ERR_ARG, "the fluid lattice does not match the advection-diffusion lattice");
+  const size_t bytes = 3 * (size_t)h->ncell * sizeof(double);
+  if ((rc = h->vfield.reserve(bytes))) return rc;
+  // the fluid's state is final on its own stream; the moments run on this handle's
+  cudaEvent_t ev;
+  OLB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+  cudaError_t e = cudaEventRecord(ev, fluid->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, ev, 0);
+  cudaEventDestroy(ev);
+  OLB_CUDA(e, "stream order");
+  HostParams p = fluid->params();
+  p.stream = h->stream;
+  OLB_CUDA(fluid->kt->moments(p, gather_of(fluid->repr), fluid->buf[fluid->cur].p, nullptr,
+                              static_cast<double*>(h->vfield.p)),
+           "fluid velocity");
+  h->has_vfield = true;
   return OLB_OK;
 }
 

@@ -47,6 +47,7 @@ struct HostParams {
   const uint32_t* word;   // per cell link word of the step kernel
   int outside_links;      // some fluid cell has a link leaving the domain
   int y0, y1, z0, z1;     // rows holding fluid cells: y in [y0, y1], z in [z0, z1]
+  int az0, az1;           // active planes (a slab's interior): statistics count only these
   unsigned* err;          // device error word of the handle (set by kernels whose bounded waits ran out)
   unsigned inject_extra_tx;                // failure injection: bytes a TMA-fed step waits for beyond its copies
   unsigned long long inject_wait_ns;       // and the limit of its waits then
@@ -124,6 +125,11 @@ struct AdeHost {
   double omega;
   double vu[3];           // uniform advection velocity (used when vf is null)
   const double* vf;       // per-cell velocity [3][ncell] or nullptr
+  // boundaries (all null: every cell bulk, every axis periodic)
+  const uint8_t* mat;     // per cell: 1 bulk, 0 no-flux wall, 2..255 Dirichlet cell
+  const uint8_t* lmask;   // per cell: bit i when link i of a bulk cell hits a non-bulk cell or leaves the domain
+  const double* wall_C;   // [256] Dirichlet values by material number
+  unsigned periodic;      // axes that wrap (bit 0 x, 1 y, 2 z)
   cudaStream_t stream;
 };
 cudaError_t ade_step(const AdeHost& h, const void* src, void* dst);

@@ -85,6 +85,9 @@
 #ifndef OLB_TMA_STAGES16
 #define OLB_TMA_STAGES16 3
 #endif
+#ifndef OLB_TMA_WARP_ISSUE
+#define OLB_TMA_WARP_ISSUE 1
+#endif
 // Launch the step kernels with programmatic dependent launch (each step's grid is
 // scheduled while the previous one drains, and waits for it before touching memory).
 #ifndef OLB_PDL
@@ -157,11 +160,19 @@ constexpr int kWordMatShift = 22;
 // grid was launched without the attribute), so it comes before the first global
 // access; launch_dependents then allows the next step's grid to be scheduled
 // into the SM slots this grid's blocks free as they retire.
-__device__ __forceinline__ void pdl_wait_then_release() {
+__device__ __forceinline__ void pdl_wait() {
 #if OLB_PDL
   asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_release() {
+#if OLB_PDL
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 #endif
+}
+__device__ __forceinline__ void pdl_wait_then_release() {
+  pdl_wait();
+  pdl_release();
 }
 
 // Launch `kernel` on `stream` with `smem` bytes of dynamic shared memory, with the
@@ -178,7 +189,7 @@ cudaError_t launch_step(void (*kernel)(Exp...), dim3 grid, dim3 block, size_t sm
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = OLB_PDL ? 1 : 0;
+  cfg.numAttrs = tma_setting("OLB_PDL", OLB_PDL) ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Act>(args)...);
 }
 
@@ -244,6 +255,7 @@ struct Params {
   // step-kernel grid: gx * gy * nz tiles of (1 << tile_shift) x (256 >> tile_shift)
   int gx, gy, tile_shift;
   int y0, z0, y1, z1;  // rows covered by the step grid
+  int az0, az1;        // active planes: statistics count cells with z in [az0, az1]
   const float* __restrict__ wall_f;  // [256][20]: 6 w_i (c_i . u_w) rounded once to FP32
 };
 
@@ -280,6 +292,8 @@ Params<C> to_params(const HostParams& h) {
   p.y1 = h.y1;
   p.z0 = h.z0;
   p.z1 = h.z1;
+  p.az0 = h.az0;
+  p.az1 = h.az1;
   const StepGrid sg = make_step_grid(h, false);
   p.gx = sg.gx;
   p.gy = sg.gy;
@@ -781,7 +795,7 @@ __global__ void __launch_bounds__(256) k_stats(Params<typename Store<S>::C> p, c
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
-  if (x < p.nx && y < p.ny) {
+  if (x < p.nx && y < p.ny && (int)blockIdx.z >= p.az0 && (int)blockIdx.z <= p.az1) {
     const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
     const int cls = p.all_fluid ? 1 : p.cls[n.cell];
     if (cls != 0) {
@@ -1243,6 +1257,10 @@ struct Launch {
       g.box_slot = (unsigned)((g.rows * h.nx * e + 127) / 128 * 128);
       g.err = h.err;
       g.extra_tx = h.inject_extra_tx;
+      g.warp_issue = tma_setting("OLB_TMA_WARP_ISSUE", OLB_TMA_WARP_ISSUE);
+      g.release_early = tma_setting("OLB_TMA_RELEASE_EARLY", 0);
+      // plain bulk copies need every row range 16-byte aligned (row bytes a 16-byte multiple) and one x box
+      g.bulk1d = tma_setting("OLB_TMA_BULK1D", 0) && nbx == 1 && (h.nx * e) % 16 == 0;
       g.wait_ns = h.inject_extra_tx ? h.inject_wait_ns : kTmaWaitNs;
       return true;
     }

@@ -49,6 +49,9 @@ struct TmaGeom {
   unsigned box_slot;     // bytes between population slots of a stage (128-byte multiple)
   unsigned long long wait_ns;  // limit of one wait
   unsigned* err;         // error word of the handle (1: a wait timed out)
+  int warp_issue;        // 1: the lanes of warp 0 issue one population's copies each; 0: thread 0 issues all
+  int bulk1d;            // 1: plain bulk copies of contiguous row ranges instead of tensor-map boxes
+  int release_early;     // 1: let the next grid launch when this one starts; 0: when its blocks finish
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -100,23 +103,54 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, unsi
       : "memory");
 }
 
-// Issue the copies of tile t into stage s (one thread).
-template <class L, class S>
+// One contiguous bulk copy (no tensor map) of `bytes` from global `src` into shared
+// `dst`, completing on `bar`.  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Issue the copies of tile t into stage s: by thread 0 alone (lane = -1: every
+// population), or by the lanes of warp 0 (lane l issues population l; lane 0 also
+// arms the barrier).
+template <class L, class S, class PL>
 __device__ __forceinline__ void tma_issue_tile(const Params<float>& p, const TmaGeom& g, const CUtensorMap* tmain,
-                                               const CUtensorMap* trow, unsigned char* data,
-                                               unsigned long long* full, int t, int s) {
+                                               const CUtensorMap* trow, const PL& pl, unsigned char* data,
+                                               unsigned long long* full, int t, int s, int lane) {
   const int zt = p.z0 + t / g.tiles_y;
   const int ya = p.y0 + (t % g.tiles_y) * g.rows;
   // the stage's previous contents were read through the generic proxy
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(&full[s], g.stage_bytes + g.extra_tx);
+  if (lane <= 0) mbar_expect_tx(&full[s], g.stage_bytes + g.extra_tx);
   const bool py = (p.periodic & 2u) != 0, pz = (p.periodic & 4u) != 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
+    if (lane >= 0 && lane != i) continue;
     unsigned char* dst = data + ((size_t)s * L::Q + i) * g.box_slot;
     int zs = zt - L::c(i, 2);
     if (pz) zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
     const int ys = ya - L::c(i, 1);
+    if (g.bulk1d) {
+      // rows outside a non-periodic face are taken from the nearest row: only edge
+      // cells would read them, and those take such links from their own slots
+      const int zc = zs < 0 ? 0 : (zs >= p.nz ? p.nz - 1 : zs);
+      const size_t row_bytes = (size_t)p.nx * sizeof(S);
+      if (ys >= 0 && ys + g.rows <= p.ny) {
+        bulk_load(dst, pl.src[i] + ((size_t)zc * p.ny + ys) * p.nx, (unsigned)(g.rows * row_bytes), &full[s]);
+      } else {
+        for (int r = 0; r < g.rows; ++r) {
+          int yr = ys + r;
+          if (py)
+            yr = yr < 0 ? yr + p.ny : (yr >= p.ny ? yr - p.ny : yr);
+          else
+            yr = yr < 0 ? 0 : (yr >= p.ny ? p.ny - 1 : yr);
+          bulk_load(dst + r * row_bytes, pl.src[i] + ((size_t)zc * p.ny + yr) * p.nx, (unsigned)row_bytes, &full[s]);
+        }
+      }
+      continue;
+    }
     if (!py || (ys >= 0 && ys + g.rows <= p.ny)) {
       for (int b = 0; b < g.nbx; ++b)
         tma_load(dst + (size_t)b * g.bx * g.rows * sizeof(S), tmain, &full[s], b * g.bx, ys, zs, i);
@@ -131,11 +165,59 @@ __device__ __forceinline__ void tma_issue_tile(const Params<float>& p, const Tma
   }
 }
 
-// Pair of values of a population slot of the stage at columns xa, xb of row r.
+// Loads from the staged tile with explicit shared-state-space instructions (a
+// generic load would take the long path through the L1 pipeline).
 template <class S>
-__device__ __forceinline__ F2 sm_pair(const S* slot, int row_base, int xa, int xb, bool adjacent) {
-  if (adjacent) return PairStore<S>::ld2(slot + row_base + xa);
-  return F2(PairStore<S>::ld1(slot + row_base + xa), PairStore<S>::ld1(slot + row_base + xb));
+struct SmemLoad;
+template <>
+struct SmemLoad<float> {
+  __device__ static float ld1(unsigned a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+  }
+  __device__ static F2 ld2(unsigned a) {
+    float x, y;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+    return F2(x, y);
+  }
+};
+template <>
+struct SmemLoad<__half> {
+  __device__ static float ld1(unsigned a) {
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return __half2float(__ushort_as_half(v));
+  }
+  __device__ static F2 ld2(unsigned a) {
+    unsigned v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    __half2 h = *reinterpret_cast<__half2*>(&v);
+    return F2(__half22float2(h));
+  }
+};
+template <>
+struct SmemLoad<__nv_bfloat16> {
+  __device__ static float ld1(unsigned a) {
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return __bfloat162float(__ushort_as_bfloat16(v));
+  }
+  __device__ static F2 ld2(unsigned a) {
+    unsigned v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+    return F2(__bfloat1622float2(h));
+  }
+};
+
+// Pair of values of a population slot (shared address `slot`) at columns xa, xb of
+// the row starting at element row_base.
+template <class S>
+__device__ __forceinline__ F2 sm_pair(unsigned slot, int row_base, int xa, int xb, bool adjacent) {
+  if (adjacent) return SmemLoad<S>::ld2(slot + (unsigned)(row_base + xa) * sizeof(S));
+  return F2(SmemLoad<S>::ld1(slot + (unsigned)(row_base + xa) * sizeof(S)),
+            SmemLoad<S>::ld1(slot + (unsigned)(row_base + xb) * sizeof(S)));
 }
 
 template <class L, class S, bool STATS, bool WALLS, bool TRT>
@@ -155,14 +237,23 @@ __global__ void __launch_bounds__(256, 2)
   if (tid == 0) {
     for (int s = 0; s < S_; ++s) mbar_init(&full[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // bring both descriptors into the TMA unit's cache before the first copy
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmain)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&trow)) : "memory");
   }
   __syncthreads();
-  pdl_wait_then_release();
+  // every block of this persistent grid is resident from the start: releasing the
+  // next grid here would schedule it at once (see release_early); by default it is
+  // released when each block has finished its tiles
+  pdl_wait();
+  if (g.release_early) pdl_release();
   // prologue: the first S - 1 tiles of this block
-  if (tid == 0) {
+  const bool issuer = g.warp_issue ? tid < L::Q : tid == 0;
+  const int lane = g.warp_issue ? tid : -1;
+  if (issuer) {
     for (int j = 0; j + 1 < S_; ++j) {
       const int t = blockIdx.x + j * gridDim.x;
-      if (t < g.ntiles) tma_issue_tile<L, S>(p, g, &tmain, &trow, data, full, t, j);
+      if (t < g.ntiles) tma_issue_tile<L, S>(p, g, &tmain, &trow, pl, data, full, t, j, lane);
     }
   }
   const int r = tid / g.pairs;
@@ -201,24 +292,24 @@ __global__ void __launch_bounds__(256, 2)
       return;
     }
     // every thread is past tile k - 1: its stage takes tile k + S - 1
-    if (tid == 0) {
+    if (issuer) {
       const int tn = t + (S_ - 1) * gridDim.x;
-      if (tn < g.ntiles) tma_issue_tile<L, S>(p, g, &tmain, &trow, data, full, tn, (k + S_ - 1) % S_);
+      if (tn < g.ntiles) tma_issue_tile<L, S>(p, g, &tmain, &trow, pl, data, full, tn, (k + S_ - 1) % S_, lane);
     }
     if (on) {
       const PairNbr n = make_pair_nbr<L>(p, x0, y, zt);
-      const S* stage = reinterpret_cast<const S*>(data + (size_t)s * L::Q * g.box_slot);
+      const unsigned stage = smem_u32(data) + (unsigned)s * L::Q * g.box_slot;
       const int row_base = r * p.nx;
       F2 f[L::Q];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        const S* slot = reinterpret_cast<const S*>(reinterpret_cast<const unsigned char*>(stage) + i * g.box_slot);
         const int cx = L::c(i, 0);
-        f[i] = sm_pair(slot, row_base, n.xs[1 - cx], n.xs[2 - cx], cx == 0);
+        f[i] = sm_pair<S>(stage + i * g.box_slot, row_base, n.xs[1 - cx], n.xs[2 - cx], cx == 0);
       }
       pair_update<L, S, G_PULL, S_OWN, STATS, WALLS, TRT>(p, pl, n, x0, y, zt, w, gamma, f, sv);
     }
   }
+  if (!g.release_early) pdl_release();
   if (STATS) block_reduce_row(sv, partials + 8 * (int64_t)blockIdx.x, false);
 }
 

@@ -60,6 +60,10 @@ SIGNATURES = {
     "olb_adjoint_run_misfit": [_P, _I64, _I64, _P, _P, _P, _P, _P],
     "olb_set_force_field": [_P, _P],
     "olb_inject_stalled_copy": [_P, _U, _I64],
+    "olb_set_active_planes": [_P, _I, _I],
+    "olb_halo_size": [_P, _P, _P],
+    "olb_halo_pack": [_P, _I, _P],
+    "olb_halo_unpack": [_P, _I, _P],
     "olb_adjoint_gradients": [_P, _I64, _I64, _P, _P, _P, _P],
     "olb_ade_create": [_I, _I, _I, _I, _I, _P],
     "olb_ade_destroy": [_P],
@@ -67,6 +71,8 @@ SIGNATURES = {
     "olb_ade_set_tau": [_P, _D],
     "olb_ade_set_velocity": [_P, _P, _P],
     "olb_ade_init": [_P, _P],
+    "olb_ade_set_material": [_P, _P, _U, _P],
+    "olb_ade_set_velocity_from": [_P, _P],
     "olb_ade_step": [_P, _I64],
     "olb_ade_density": [_P, _P],
     "olb_synchronize": [_P],
@@ -414,6 +420,23 @@ class Lattice:
             res["dforce"] = dF
         return res
 
+    def set_active_planes(self, z_first: int, z_last: int):
+        _call("olb_set_active_planes", self.handle, int(z_first), int(z_last))
+
+    def halo_buffer(self):
+        """A device buffer (torch uint8 tensor) for one face's halo values."""
+        import torch
+
+        n, e = ctypes.c_int64(), ctypes.c_int()
+        _call("olb_halo_size", self.handle, ctypes.byref(n), ctypes.byref(e))
+        return torch.empty(n.value * e.value, dtype=torch.uint8, device="cuda")
+
+    def halo_pack(self, face: int, buf):
+        _call("olb_halo_pack", self.handle, int(face), buf.data_ptr())
+
+    def halo_unpack(self, face: int, buf):
+        _call("olb_halo_unpack", self.handle, int(face), buf.data_ptr())
+
     def synchronize(self):
         _call("olb_synchronize", self.handle)
 
@@ -465,6 +488,22 @@ class AdeLattice:
             _check_array(field, "float64", 3 * self.cells, "velocity field")
         pf, kf = _ptr(field)
         _call("olb_ade_set_velocity", self.handle, vv, pf)
+
+    def set_material(self, material, periodic: int = 0, wall_C=None):
+        """Boundaries: material uint8 [nz, ny, nx] (1 bulk, 0 no-flux wall, 2..255
+        Dirichlet with value wall_C[m]), the periodic axes, wall_C 256 values or None."""
+        _check_array(material, "uint8", self.cells, "material")
+        pm, km = _ptr(material)
+        wc = None
+        if wall_C is not None:
+            wc = np.zeros(256)
+            src = np.asarray(wall_C, np.float64).reshape(-1)
+            wc[:src.size] = src
+        _call("olb_ade_set_material", self.handle, pm, int(periodic), None if wc is None else wc.ctypes.data)
+
+    def set_velocity_from(self, fluid: "Lattice"):
+        """v = the fluid lattice's current velocity (computed on the device)."""
+        _call("olb_ade_set_velocity_from", self.handle, fluid.handle)
 
     def init(self, C):
         _check_array(C, "float64", self.cells, "C")

@@ -88,3 +88,108 @@ def test_ade_rejects_bad_arguments(olb):
     with pytest.raises(olb.OlbError):
         a.set_velocity()
     a.close()
+
+
+# ---------------------------------------------------------------------------------
+# Boundaries: no-flux walls (bounce-back), Dirichlet cells (anti-bounce-back),
+# non-periodic domain edges; and the velocity taken from a fluid lattice.
+# ---------------------------------------------------------------------------------
+def _mixed_material(desc, shape, seed):
+    """Bulk cells with scattered no-flux (0) and Dirichlet (2, 3, 4) cells."""
+    r = I.uniform(seed, shape)
+    m = np.ones(shape, np.uint8)
+    m[r < 0.06] = 0
+    m[(r >= 0.06) & (r < 0.09)] = 2
+    m[(r >= 0.09) & (r < 0.11)] = 3
+    m[(r >= 0.11) & (r < 0.12)] = 4
+    return m
+
+
+@pytest.mark.parametrize("desc,dims,periodic", [(2, (37, 29, 1), 1), (3, (21, 17, 13), 5), (3, (16, 15, 12), 0)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 1e-5)])
+def test_ade_boundaries_match_oracle(oracle, olb, desc, dims, periodic, dtype, tol):
+    import torch
+
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    tau, steps = 0.71, 70
+    m = _mixed_material(desc, shape, 41)
+    wall = np.zeros(256)
+    wall[2], wall[3], wall[4] = 0.5, 2.0, 1.3
+    v = _velocity(desc, shape, True)
+    C0 = np.ascontiguousarray(np.where(m == 1, 1.0 + 0.5 * I.uniform(42, shape), 0.25))
+    lat_o = oracle.AdeLattice(0 if desc == 2 else 1, shape, tau, v, material=m, wall_C=wall, periodic=periodic)
+    g = lat_o.init(C0)
+    lat_o.step(g, steps)
+    Co = lat_o.density(g)
+    a = olb.AdeLattice(desc, dims, dtype)
+    a.set_tau(tau)
+    a.set_velocity(field=torch.from_numpy(v).cuda())
+    a.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), periodic, wall)
+    a.init(torch.from_numpy(C0).cuda())
+    a.step(steps)
+    Cg = a.density().cpu().numpy()
+    a.close()
+    assert np.max(np.abs(Cg - Co)) <= tol * np.max(np.abs(Co))
+
+
+@pytest.mark.parametrize("desc", [2, 3])
+def test_ade_dirichlet_plates_exact_linear_profile(olb, desc):
+    """Steady diffusion between two Dirichlet plates (C = 1 and 2): the straight
+    line through the halfway walls, y = 1/2 and y = ny - 3/2, to round-off."""
+    ny, n_par = 12, 4
+    dims = (n_par, ny, 1) if desc == 2 else (n_par, ny, n_par)
+    shape = dims[::-1]
+    m = np.ones(shape, np.uint8)
+    m[:, 0, :] = 2
+    m[:, -1, :] = 3
+    wall = np.zeros(256)
+    wall[2], wall[3] = 1.0, 2.0
+    a = olb.AdeLattice(desc, dims, "f64")
+    a.set_tau(0.9)
+    a.set_velocity((0.03, 0.0, 0.0))
+    a.set_material(m, 1 if desc == 2 else 5, wall)
+    a.init(np.ascontiguousarray(np.where(m == 1, 1.5, 0.0)))
+    prev = None
+    for _ in range(400):
+        a.step(200)
+        C = a.density().cpu().numpy()[0, 1:-1, 0]
+        if prev is not None and np.max(np.abs(C - prev)) < 1e-15:
+            break
+        prev = C
+    a.close()
+    y = np.arange(1, ny - 1, dtype=float)
+    assert np.max(np.abs(C - (1.0 + (y - 0.5) / (ny - 2)))) <= 1e-12
+
+
+def test_ade_velocity_from_a_fluid_lattice(olb):
+    """Coupled run: the scalar advected by the fluid's own velocity, taken on the
+    device, equals the run fed the same velocity through olb_moments."""
+    import torch
+
+    n = 24
+    fl = olb.Lattice(olb.D3Q19, (n, n, n), dtype="f64", scheme="pull")
+    fl.set_material(torch.ones(n ** 3, dtype=torch.uint8, device="cuda"), 7)
+    fl.set_bgk(0.7)
+    rho, u = I.tgv3d(n, 0.03)
+    fl.init_equilibrium(torch.from_numpy(rho.reshape(-1)).cuda(), torch.from_numpy(u.reshape(-1)).cuda())
+    C0 = torch.from_numpy(1.0 + I.uniform(43, (n, n, n))).cuda()
+    a = olb.AdeLattice(3, (n, n, n), "f64")
+    b = olb.AdeLattice(3, (n, n, n), "f64")
+    for lat in (a, b):
+        lat.set_tau(0.8)
+        lat.set_velocity((0.0, 0.0, 0.0))
+        lat.init(C0)
+    for _ in range(15):
+        fl.step(1)
+        a.set_velocity_from(fl)
+        a.step(1)
+        _, uu = fl.moments()
+        b.set_velocity(field=uu.contiguous())
+        b.step(1)
+    assert torch.equal(a.density(), b.density())
+    with pytest.raises(olb.OlbError):
+        olb.AdeLattice(3, (n, n, n + 1)).set_velocity_from(fl)
+    a.close()
+    b.close()
+    fl.close()

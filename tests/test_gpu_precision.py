@@ -72,9 +72,12 @@ def test_storage_precision_tgv3d_64_5000_steps(olb, record_property):
     (tests/golden/tgv3d64_oracle.npz, written by tests/golden/make_tgv3d64.py).
 
     Two normalisations: ||u - u_oracle|| / ||u_oracle|| and the RMS error over u0.
-    The strict ratio divides by a signal that has decayed by up to exp(-4.8) at
-    tau = 0.6, so it amplifies storage noise; FP16 meets 1e-3 in it while the
-    vortex keeps most of its energy (tau 0.51, 0.52) and 1e-3 of u0 everywhere."""
+    The same bounds hold at every tau.  FP16 stays within 1e-3 of u0 everywhere; in
+    the strict ratio it reaches 7e-4 and 4e-4 at tau 0.51 and 0.52 but 1.2e-3 and
+    3.0e-3 at tau 0.55 and 0.6, where the signal has decayed by up to exp(-4.8) and
+    the ratio carries the random walk of 11-bit rounding over the mode's lifetime.
+    That is a miss against the benchmark spec's bound of 1e-3 relative at those two
+    tau, recorded as such; the test bounds the strict ratio at 5e-3."""
     import os
 
     import torch
@@ -106,6 +109,5 @@ def test_storage_precision_tgv3d_64_5000_steps(olb, record_property):
         assert errs["f64"][0] <= 1e-10
         assert errs["f32"][0] <= 1e-3 and errs["f32"][1] <= 1e-4
         assert errs["f16"][1] <= 1e-3
-        if tau <= 0.52:
-            assert errs["f16"][0] <= 1e-3
+        assert errs["f16"][0] <= 5e-3
         assert errs["bf16"][0] <= 5e-2 and errs["bf16"][1] <= 1e-2
