@@ -44,6 +44,9 @@ LID = 0.05
 TAU = I.cavity_tau(N_SIDE, 400.0, LID)
 SEED = 1
 METRIC = "MLUPS"
+# GB300 HBM3e bandwidth as specified (the roofline's `peak` is the measured copy bandwidth instead; kernels here
+# reach slightly above that copy figure on large all-fluid lattices, so both fractions are reported)
+NOMINAL_HBM_GBS = 7900.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 
 
@@ -338,11 +341,14 @@ def porous_channel(olb, torch, nx, ny, nz, dtype, tau=0.8):
     return lat, m
 
 
-def experiment_adjoint384(torch, olb, fd_cells=4):
+def experiment_adjoint384(torch, olb, fd_cells=64, h=1e-3):
     """Adjoint at scale: channel 384x192x192, FP16 state (FP32 arithmetic, FP64
-    gradient), 4000 steps, checkpoints every 200; compared with the FP32-storage
-    adjoint (checkpoints every 100) and with central differences of FP64 forward
-    runs at `fd_cells` seeded fluid cells (h = 1e-5) and tau (h = 1e-6)."""
+    gradient), 4000 steps, checkpoints every 200; compared per cell with the
+    FP32-storage adjoint (checkpoints every 100) at every fluid cell, and both with
+    central differences of FP64 forward runs at `fd_cells` seeded fluid cells
+    (h = 1e-3 for gamma, the step experiment_fd256 explains) and tau (h = 1e-6).
+    An FP64-storage adjoint does not fit at this size (the segment of 200 states
+    alone would take 430 GB)."""
     nx, ny, nz, steps = 384, 192, 192, 4000
     obj = (0, nx - 1, 0)
     res = {"workload": "channel 384x192x192, 4000 steps, loss = mean u_x on x = 383"}
@@ -357,15 +363,19 @@ def experiment_adjoint384(torch, olb, fd_cells=4):
         fl = int((m == I.FLUID).sum())
         grads[dtype] = (loss, dg.cpu().numpy().reshape(-1), dtau)
         res[dtype] = {"K": K, "seconds": round(sec, 2), "MLUPS": round(fl * steps / sec / 1e6, 1),
-                      "loss": loss, "dL_dtau": dtau, "grad_l2": float(np.linalg.norm(grads[dtype][1]))}
+                      "loss": loss, "dL_dtau": dtau}
         lat.close()
         del dg
         torch.cuda.empty_cache()
     g16, g32 = grads["f16"][1], grads["f32"][1]
-    res["f16_vs_f32_grad_rel_l2"] = float(np.linalg.norm(g16 - g32) / np.linalg.norm(g32))
+    flm = (m == I.FLUID).reshape(-1)
+    r = np.abs(g16[flm] - g32[flm]) / np.abs(g32[flm])
+    res["f16_vs_f32_all_fluid_cells"] = {
+        "rel_l2": float(np.linalg.norm(g16[flm] - g32[flm]) / np.linalg.norm(g32[flm])),
+        "rel_median": float(np.median(r)), "rel_p99": float(np.quantile(r, 0.99)),
+        "abs_max_over_max_gradient": float(np.abs(g16[flm] - g32[flm]).max() / np.abs(g32[flm]).max())}
     res["f16_vs_f32_dtau_rel"] = abs(grads["f16"][2] - grads["f32"][2]) / abs(grads["f32"][2])
     # FP64 central differences
-    m = I.channel(nx, ny, nz)
     gamma = I.smoothed_porosity(2, m)
     ref = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype="f64", scheme="pull")
     ref.set_material(torch.from_numpy(m.reshape(-1).copy()).cuda(), 1)
@@ -380,18 +390,26 @@ def experiment_adjoint384(torch, olb, fd_cells=4):
         _, u = ref.moments()
         return float(u[0, :, :, nx - 1][plane].mean())
 
+    t = time.perf_counter()
+    sel = I.random_fluid_cells(3, m, fd_cells)
     fd = []
-    for c in I.random_fluid_cells(3, m, fd_cells):
+    for c in sel:
         gp = gamma.reshape(-1).copy()
         gm = gp.copy()
-        gp[c] += 1e-5
-        gm[c] -= 1e-5
-        d = (run(gp, 0.8) - run(gm, 0.8)) / 2e-5
-        fd.append({"cell": int(c), "fd": d, "f16_rel": abs(g16[c] - d) / abs(d), "f32_rel": abs(g32[c] - d) / abs(d)})
-    d = (run(gamma, 0.8 + 1e-6) - run(gamma, 0.8 - 1e-6)) / 2e-6
-    res["fd"] = fd
-    res["fd_dtau"] = {"fd": d, "f16_rel": abs(grads["f16"][2] - d) / abs(d), "f32_rel": abs(grads["f32"][2] - d) / abs(d)}
+        gp[c] += h
+        gm[c] -= h
+        fd.append((run(gp, 0.8) - run(gm, 0.8)) / (2 * h))
+    fd = np.array(fd)
+    d_tau = (run(gamma, 0.8 + 1e-6) - run(gamma, 0.8 - 1e-6)) / 2e-6
     ref.close()
+    for key, g in (("f16", g16), ("f32", g32)):
+        rel = np.abs(g[sel] - fd) / np.abs(fd)
+        res[f"{key}_vs_fd"] = {"cells": int(len(sel)), "h_gamma": h, "rel_max": float(rel.max()),
+                               "rel_median": float(np.median(rel)),
+                               "cells_within_1e-4": int((rel <= 1e-4).sum()),
+                               "cells_within_1e-3": int((rel <= 1e-3).sum()),
+                               "dtau_rel": abs(grads[key][2] - d_tau) / abs(d_tau)}
+    res["fd_seconds"] = round(time.perf_counter() - t, 1)
     return res
 
 
@@ -652,6 +670,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_step_pair<D3Q19,float,G_PULL,S_OWN>", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "traffic": None if traffic is None else round(traffic),
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": round(kernel_ms, 5)},

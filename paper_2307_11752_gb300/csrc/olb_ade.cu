@@ -100,7 +100,8 @@ __device__ __forceinline__ void velocity(const AdeParams<T>& p, int64_t c, T (&v
   for (int a = 0; a < 3; ++a) v[a] = p.vf ? (T)p.vf[a * p.n + c] : p.vu[a];
 }
 
-template <class L, class T>
+// BC = false: every cell bulk, every axis periodic (no mask, material or wall code).
+template <class L, class T, bool BC>
 __global__ void __launch_bounds__(256) k_ade_step(AdeParams<T> p, const T* __restrict__ src, T* __restrict__ dst) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.n) return;
@@ -115,11 +116,14 @@ __global__ void __launch_bounds__(256) k_ade_step(AdeParams<T> p, const T* __res
     g[i] = src[i * p.n + c];
     C += g[i];
   }
-  const unsigned links = p.lmask ? p.lmask[c] : 0u;
-  if (p.mat && p.mat[c] != 1) {  // non-bulk cells keep their values
+  unsigned links = 0u;
+  if (BC) {
+    links = p.lmask[c];
+    if (p.mat[c] != 1) {  // non-bulk cells keep their values
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) dst[i * p.n + c] = g[i];
-    return;
+      for (int i = 0; i < L::Q; ++i) dst[i * p.n + c] = g[i];
+      return;
+    }
   }
   T v[3], geq[L::Q];
   velocity(p, c, v);
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(256) k_ade_step(AdeParams<T> p, const T* __res
   for (int i = 0; i < L::Q; ++i) {
     const T gs = g[i] - p.omega * (g[i] - geq[i]);
     const int64_t t = ((int64_t)zs[1 + L::c(i, 2)] * p.ny + ys[1 + L::c(i, 1)]) * p.nx + xs[1 + L::c(i, 0)];
-    if (!(links & (1u << i))) {
+    if (!BC || !(links & (1u << i))) {
       dst[i * p.n + t] = gs;
       continue;
     }
@@ -178,8 +182,12 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 template <class L, class T>
 cudaError_t step_t(const AdeHost& h, const void* src, void* dst) {
-  k_ade_step<L, T><<<blocks_for(h.ncell), 256, 0, h.stream>>>(to_params<T>(h), static_cast<const T*>(src),
-                                                                static_cast<T*>(dst));
+  if (h.mat)
+    k_ade_step<L, T, true><<<blocks_for(h.ncell), 256, 0, h.stream>>>(to_params<T>(h), static_cast<const T*>(src),
+                                                                        static_cast<T*>(dst));
+  else
+    k_ade_step<L, T, false><<<blocks_for(h.ncell), 256, 0, h.stream>>>(to_params<T>(h), static_cast<const T*>(src),
+                                                                         static_cast<T*>(dst));
   return cudaGetLastError();
 }
 

@@ -927,6 +927,7 @@ __global__ void __launch_bounds__(256) k_adjoint(Params<typename Store<S>::C> p,
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const size_t N = (size_t)p.pitch;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
+  pdl_wait_then_release();  // launched like the step kernels (the sweep alternates them)
   if (x < p.nx && y < p.ny) {
     const Nbr n = make_nbr<L>(p, x, y, blockIdx.z);
     const int cls = p.all_fluid ? 1 : p.cls[n.cell];
@@ -1471,14 +1472,12 @@ struct Launch {
     const T* li = static_cast<const T*>(lam_in);
     T* lo = static_cast<T*>(lam_out);
     if (gather == G_OWN)
-      k_adjoint<L, S, G_OWN, TRT><<<g.grid, g.block, 0, h.stream>>>(params(h), st, li, lo, dgamma, dforce,
-                                                                      partials);
-    else if (gather == G_PULL)
-      k_adjoint<L, S, G_PULL, TRT><<<g.grid, g.block, 0, h.stream>>>(params(h), st, li, lo, dgamma, dforce,
-                                                                       partials);
-    else
-      return cudaErrorInvalidValue;
-    return cudaGetLastError();
+      return launch_step(k_adjoint<L, S, G_OWN, TRT>, g.grid, g.block, 0, h.stream, params(h), st, li, lo, dgamma,
+                         dforce, partials);
+    if (gather == G_PULL)
+      return launch_step(k_adjoint<L, S, G_PULL, TRT>, g.grid, g.block, 0, h.stream, params(h), st, li, lo, dgamma,
+                         dforce, partials);
+    return cudaErrorInvalidValue;
   }
   static cudaError_t adjoint(const HostParams& h, int gather, const void* state,
                              const void* lam_in, void* lam_out, double* dgamma, double* dforce,

@@ -155,7 +155,8 @@ def test_channel_384_block_continuation_f16(oracle, olb):
 def test_adjoint_channel256_per_cell_against_differences(olb):
     """FP32- and FP64-storage adjoints on the 256 x 128 x 128 porous channel (300
     steps, K = 50) against central differences of FP64 GPU forward runs at 8 seeded
-    fluid cells and tau, per cell and with no absolute slack: FP64 within 1e-6, FP32
+    fluid cells and tau, per cell and with no absolute slack: FP64 within 1e-5 (the resolution of the
+    differences at the smallest sampled gradient), FP32
     within 1e-4 relative.  The gradients are 1e-13 .. 1e-11 against a loss of ~4e-6,
     so the step is h = 1e-3 (at 1e-5 the two losses share all but their last few
     digits), and the quotients at h and h/2 are combined by Richardson extrapolation,
@@ -170,6 +171,8 @@ def test_adjoint_channel256_per_cell_against_differences(olb):
     F = (I.channel_force(ny, tau), 0.0, 0.0)
     steps, K = 300, 50
     obj = (0, nx - 1, 0)
+    # FP64: 1e-5, the differences' own resolution at the smallest sampled gradient
+    # (rounding noise ~ eps |L| / (h |dL/dgamma|) = 1e-16 * 4e-6 / (5e-4 * 1.6e-13) ~ 5e-6)
 
     def lattice(dt):
         lat = olb.Lattice(olb.D3Q19, (nx, ny, nz), dtype=dt, scheme="pull")
@@ -214,7 +217,7 @@ def test_adjoint_channel256_per_cell_against_differences(olb):
     cells = I.random_fluid_cells(3, near, 8)
     fd = [(4 * quotient(c, h / 2) - quotient(c, h)) / 3 for c in cells]
     for c, d in zip(cells, fd):
-        assert abs(grads["f64"][0][c] - d) <= 1e-6 * abs(d), (c, d, grads["f64"][0][c])
+        assert abs(grads["f64"][0][c] - d) <= 1e-5 * abs(d), (c, d, grads["f64"][0][c])
         assert abs(grads["f32"][0][c] - d) <= 1e-4 * abs(d), (c, d, grads["f32"][0][c])
     ht = 1e-6
     d = (run(gamma, tau + ht) - run(gamma, tau - ht)) / (2 * ht)
