@@ -58,6 +58,9 @@
 #ifndef OLB_PAIR16_WALLS_MIN_BLOCKS
 #define OLB_PAIR16_WALLS_MIN_BLOCKS 4
 #endif
+#ifndef OLB_PAIR16_TRT_MIN_BLOCKS
+#define OLB_PAIR16_TRT_MIN_BLOCKS 4
+#endif
 // Order and addressing of the bounce-back stores of the paired kernel, per storage
 // width: FIRST = before the own-slot stores (fewer live registers), COORDS = the
 // target index rebuilt from the coordinates instead of kept from the loads.
@@ -1305,7 +1308,7 @@ struct Launch {
       struct MapEntry {
         const void* src = nullptr;
         int nx = 0, ny = 0, nz = 0, pitch = 0, bx = 0, rows = 0;
-        alignas(64) CUtensorMap tmain, trow;
+        CUtensorMap tmain, trow;  // the type carries its 64-byte alignment
       };
       static thread_local MapEntry cache[4];
       static thread_local int next = 0;

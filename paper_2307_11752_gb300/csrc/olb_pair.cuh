@@ -44,6 +44,7 @@ struct PairStore<float> {
   static constexpr float SCALE = 1.0f;
   static constexpr int MIN_BLOCKS = OLB_PAIR_MIN_BLOCKS;
   static constexpr int MIN_BLOCKS_WALLS = OLB_PAIR_MIN_BLOCKS;
+  static constexpr int MIN_BLOCKS_TRT = OLB_PAIR_MIN_BLOCKS;
   static constexpr bool GHOST_FIRST = OLB_GHOST_FIRST32;
   static constexpr bool GHOST_COORDS = OLB_GHOST_COORDS32;
   __device__ static float ld1(const float* p) { return *p; }
@@ -56,6 +57,7 @@ struct PairStore<__half> {
   static constexpr float SCALE = Store<__half>::kScale;
   static constexpr int MIN_BLOCKS = OLB_PAIR16_MIN_BLOCKS;
   static constexpr int MIN_BLOCKS_WALLS = OLB_PAIR16_WALLS_MIN_BLOCKS;
+  static constexpr int MIN_BLOCKS_TRT = OLB_PAIR16_TRT_MIN_BLOCKS;
   static constexpr bool GHOST_FIRST = OLB_GHOST_FIRST16;
   static constexpr bool GHOST_COORDS = OLB_GHOST_COORDS16;
   __device__ static float ld1(const __half* p) { return __half2float(*p); }
@@ -68,6 +70,7 @@ struct PairStore<__nv_bfloat16> {
   static constexpr float SCALE = 1.0f;
   static constexpr int MIN_BLOCKS = OLB_PAIR16_MIN_BLOCKS;
   static constexpr int MIN_BLOCKS_WALLS = OLB_PAIR16_WALLS_MIN_BLOCKS;
+  static constexpr int MIN_BLOCKS_TRT = OLB_PAIR16_TRT_MIN_BLOCKS;
   static constexpr bool GHOST_FIRST = OLB_GHOST_FIRST16;
   static constexpr bool GHOST_COORDS = OLB_GHOST_COORDS16;
   __device__ static float ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
@@ -305,9 +308,34 @@ __device__ __forceinline__ int wrapped_cell(const Params<float>& p, int x, int y
   return (zt * p.ny + yt) * p.nx + xt;
 }
 
+// The push half step of the AA pattern stores to the neighbours: with 16-bit
+// storage (64 registers) it rebuilds their indices from the coordinates after the
+// collision rather than keeping them live across it.
+#ifndef OLB_PUSH_RENBR16
+#define OLB_PUSH_RENBR16 1
+#endif
+#ifndef OLB_PUSH_RENBR32
+#define OLB_PUSH_RENBR32 0
+#endif
+
+// A copy of v that the compiler cannot prove equal to v and cannot compute before
+// `after` (so that values derived from it are recomputed there, not kept live
+// from before).
+__device__ __forceinline__ int opaque(int v, float after) {
+  asm volatile("" : "+r"(v) : "f"(after));
+  return v;
+}
+
 // Special store paths for pairs at walls on the x faces (see the store phase).
 #ifndef OLB_XWALL_PAIRS
 #define OLB_XWALL_PAIRS 1
+#endif
+// Bounce-back stores of such pairs inside the own-slot loop (pull pattern).
+#ifndef OLB_XWALL_GHOST16
+#define OLB_XWALL_GHOST16 1
+#endif
+#ifndef OLB_XWALL_GHOST32
+#define OLB_XWALL_GHOST32 1
 #endif
 
 // Link bits of the directions with c_x == cx (all non-rest directions for cx == 0
@@ -403,8 +431,20 @@ __device__ __forceinline__ void pair_update(const Params<float>& p, const P& pl,
     // it tests only those.  These slots are never among the own slots stored
     // below (see above), so the bounce-back stores go first: the own-slot stores
     // then release the post-collision values one by one.
-    const uint32_t l0 = fl0 ? nb0 : 0u;
-    const uint32_t l1 = fl1 ? nb1 : 0u;
+    //
+    // In such a pair the fluid cell's links usually point at the x wall only.  Its
+    // bounce-back targets are then the wall cells (x_wall, y + c_y, z + c_z), at a
+    // fixed offset from its own index when y and z are not on a domain face (no
+    // wrap-around).  Those stores go into the own-slot loop below as predicated
+    // stores, so that the one boundary pair of a warp does not diverge from the
+    // others; every other bounce-back link takes the per-cell path.
+    bool interior = (unsigned)(y - 1) < (unsigned)(p.ny - 2);
+    if (L::DIM == 3) interior = interior && (unsigned)(z - 1) < (unsigned)(p.nz - 2);
+    constexpr bool XG = sizeof(S) == 2 ? OLB_XWALL_GHOST16 : OLB_XWALL_GHOST32;
+    const bool lo_g = XG && lo && interior && !(nb1 & ~dir_mask<L>(-1)) && !(w[1] & kWordMoving);
+    const bool hi_g = XG && hi && interior && !(nb0 & ~dir_mask<L>(1)) && !(w[0] & kWordMoving);
+    const uint32_t l0 = (fl0 && !hi_g) ? nb0 : 0u;
+    const uint32_t l1 = (fl1 && !lo_g) ? nb1 : 0u;
     auto bounce_back = [&]() {
     if (l0 | l1) {
 #pragma unroll
@@ -437,6 +477,17 @@ __device__ __forceinline__ void pair_update(const Params<float>& p, const P& pl,
         } else {
           PairStore<S>::st2(q, f[i]);
         }
+        if (XG && L::c(i, 0) != 0) {
+          // the x-wall bounce-back of this direction: cell x0 + 1 of a lo pair along
+          // c_x = -1, cell x0 of a hi pair along c_x = +1, into slot opp(i) (S_OWN) of
+          // the wall cell x + c_i
+          const bool on = L::c(i, 0) == -1 ? (lo_g && ((nb1 >> i) & 1u)) : (hi_g && ((nb0 >> i) & 1u));
+          if (on) {
+            const int off = (L::c(i, 0) == -1 ? 0 : 1) + L::c(i, 1) * p.nx + (L::DIM == 3 ? L::c(i, 2) * p.nx * p.ny : 0);
+            PairStore<S>::st1(pl.dst[(SC == S_OWN) ? opp<L>(i) : i] + cell + off,
+                              L::c(i, 0) == -1 ? f[i].v.y : f[i].v.x);
+          }
+        }
       }
     } else {
 #pragma unroll
@@ -461,10 +512,45 @@ __device__ __forceinline__ void pair_update(const Params<float>& p, const P& pl,
       }
     }
   } else {  // S_PUSH
-    const bool plain = fl0 && fl1 && !((w[0] | w[1]) & (kWordLinks | kWordMoving)) && !edge[0] && !edge[1];
-    if (plain) {
+    constexpr bool RENBR = sizeof(S) == 2 ? OLB_PUSH_RENBR16 : OLB_PUSH_RENBR32;
+    const PairNbr m = RENBR ? make_pair_nbr<L>(p, opaque(x0, f[0].v.x), opaque(y, f[0].v.x), opaque(z, f[0].v.x)) : n;
+    const uint32_t lk0 = w[0] & (kWordLinks | kWordMoving), lk1 = w[1] & (kWordLinks | kWordMoving);
+    const bool plain = fl0 && fl1 && !(lk0 | lk1) && !edge[0] && !edge[1];
+    // A pair at a wall on an x face: one cell non-fluid with fluid neighbours only on
+    // its partner's side, the fluid cell with wall links only in the directions that
+    // point at the wall's side (no moving wall, no domain edge).  In this half step
+    // every slot is read and written by one cell only.  The non-fluid cell's values may
+    // then go with its partner's paired stores in the directions with c_x = 0: the
+    // slots they reach are non-fluid cells' and read by the non-fluid cell alone.  Not
+    // along c_x = +-1, where they could hit a fluid cell's own bounce-back slot.  The
+    // fluid cell's wall links store in its own slots.  Such pairs take the plain store
+    // sequence with predicated stores and selected addresses, so a warp holding one
+    // does not diverge.
+    const uint32_t nb0 = w[0] & kWordLinks, nb1 = w[1] & kWordLinks;  // non-fluid cells: fluid neighbours
+    const bool lo = OLB_XWALL_PAIRS && !fl0 && fl1 && !(nb0 & ~dir_mask<L>(1)) && !(lk1 & ~dir_mask<L>(-1)) &&
+                    !edge[1];
+    const bool hi = OLB_XWALL_PAIRS && fl0 && !fl1 && !(nb1 & ~dir_mask<L>(-1)) && !(lk0 & ~dir_mask<L>(1)) &&
+                    !edge[0];
+    if (plain || lo || hi) {
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) st_pair(pl.dst[i], n, L::c(i, 0), L::c(i, 1), L::c(i, 2), f[i]);
+      for (int i = 0; i < L::Q; ++i) {
+        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        if (cx == 0) {
+          st_pair(pl.dst[i], m, 0, cy, cz, f[i]);
+        } else if (cx == 1) {
+          // cell x0 streams to x0 + 1 (or, in a hi pair, bounces into its own slot);
+          // cell x0 + 1 streams to x0 + 2 (not in a hi pair: it is the wall)
+          S* a = (hi && ((lk0 >> i) & 1u)) ? pl.dst[opp<L>(i)] + cell : pl.dst[i] + m.at(2, cy, cz);
+          if (!lo) PairStore<S>::st1(a, f[i].v.x);
+          if (!hi) PairStore<S>::st1(pl.dst[i] + m.at(3, cy, cz), f[i].v.y);
+        } else {
+          // cell x0 streams to x0 - 1 (not in a lo pair); cell x0 + 1 streams to x0 (or,
+          // in a lo pair, bounces into its own slot)
+          if (!lo) PairStore<S>::st1(pl.dst[i] + m.at(0, cy, cz), f[i].v.x);
+          S* b = (lo && ((lk1 >> i) & 1u)) ? pl.dst[opp<L>(i)] + cell + 1 : pl.dst[i] + m.at(1, cy, cz);
+          if (!hi) PairStore<S>::st1(b, f[i].v.y);
+        }
+      }
     } else {
       // per cell, with bounce-back links, domain edges and non-fluid cells
 #pragma unroll
@@ -487,11 +573,11 @@ __device__ __forceinline__ void pair_update(const Params<float>& p, const P& pl,
               float bounced = fi;
               float t;
               if (wall && (wd & kWordMoving) &&
-                  moving_term<L>(p, n.at(tx, L::c(i, 1), L::c(i, 2)), i, wd, t))
+                  moving_term<L>(p, m.at(tx, L::c(i, 1), L::c(i, 2)), i, wd, t))
                 bounced -= rh * t;
               PairStore<S>::st1(pl.dst[opp<L>(i)] + c, bounced);
             } else {
-              PairStore<S>::st1(pl.dst[i] + n.at(tx, L::c(i, 1), L::c(i, 2)), fi);
+              PairStore<S>::st1(pl.dst[i] + m.at(tx, L::c(i, 1), L::c(i, 2)), fi);
             }
           }
         } else if (OLB_SOLID_FILL) {
@@ -530,9 +616,9 @@ __device__ __forceinline__ void pair_update(const Params<float>& p, const P& pl,
 // the boundary paths cannot cost registers or scheduling freedom there.
 // ---------------------------------------------------------------------------------
 template <class L, class S, int G, int SC, bool STATS, bool WALLS, bool TRT>
-__global__ void __launch_bounds__(256, WALLS ? PairStore<S>::MIN_BLOCKS_WALLS : PairStore<S>::MIN_BLOCKS) k_step_pair(Params<float> p,
-                                                                             const __grid_constant__ Planes<S, WALLS> pl,
-                                                                             double* partials) {
+__global__ void __launch_bounds__(256, TRT ? PairStore<S>::MIN_BLOCKS_TRT
+                                            : (WALLS ? PairStore<S>::MIN_BLOCKS_WALLS : PairStore<S>::MIN_BLOCKS))
+    k_step_pair(Params<float> p, const __grid_constant__ Planes<S, WALLS> pl, double* partials) {
   float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int tid = threadIdx.x;
   pdl_wait_then_release();
