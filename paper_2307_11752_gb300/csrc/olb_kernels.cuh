@@ -33,15 +33,31 @@
 
 #include "olb_internal.h"
 
+// The generic (one cell per thread) BGK collision with omega w_k folded into the
+// equilibrium's coefficients per weight class: fewer arithmetic instructions, which
+// is what bounds the FP64 step on this GPU.
+#ifndef OLB_FOLD_OMEGA_GENERIC
+#define OLB_FOLD_OMEGA_GENERIC 1
+#endif
 // Resident blocks of 256 threads per SM that the step kernel is compiled for
 // (bounds its registers: 65536 / (256 * blocks)).
 #ifndef OLB_STEP_MIN_BLOCKS
 #define OLB_STEP_MIN_BLOCKS 4
 #endif
+// FP64: 2 blocks (<= 128 registers, no spill; at 4 blocks it spills ~390 bytes per
+// thread).  The FP64 step is bound by the FP64 pipe, which 16 warps per SM keep busy.
+#ifndef OLB_STEP64_MIN_BLOCKS
+#define OLB_STEP64_MIN_BLOCKS 2
+#endif
 // Same for the two-cells-per-thread step kernel (FP32 arithmetic), for FP32
 // storage and for 16-bit storage (which needs more cells in flight per byte).
+// FP32: 3 blocks (<= 80 registers) with the bounce-back stores first and their
+// targets rebuilt from the coordinates (below).  Measured at 128^3 against 2
+// blocks (128 registers, stores last): cavity pull 50.4 against 52.2 us, AA 55.3
+// against 59.3 us (mean of the two half steps), TRT 50.8 against 53.2 us, the
+// all-fluid box 47.5 against 48.6 us.
 #ifndef OLB_PAIR_MIN_BLOCKS
-#define OLB_PAIR_MIN_BLOCKS 2
+#define OLB_PAIR_MIN_BLOCKS 3
 #endif
 // Use the boundary-capable instance of the paired kernel on every lattice (for
 // measuring what the boundary code costs on lattices without walls).
@@ -58,8 +74,10 @@
 #ifndef OLB_PAIR16_WALLS_MIN_BLOCKS
 #define OLB_PAIR16_WALLS_MIN_BLOCKS 4
 #endif
+// The TRT instances at 3 blocks (<= 80 registers): at 4 they spill 212 bytes per
+// thread; on the 128^3 cavity 37.8 against 44.2 us.
 #ifndef OLB_PAIR16_TRT_MIN_BLOCKS
-#define OLB_PAIR16_TRT_MIN_BLOCKS 4
+#define OLB_PAIR16_TRT_MIN_BLOCKS 3
 #endif
 // Order and addressing of the bounce-back stores of the paired kernel, per storage
 // width: FIRST = before the own-slot stores (fewer live registers), COORDS = the
@@ -71,10 +89,10 @@
 #define OLB_GHOST_COORDS16 1
 #endif
 #ifndef OLB_GHOST_FIRST32
-#define OLB_GHOST_FIRST32 0
+#define OLB_GHOST_FIRST32 1
 #endif
 #ifndef OLB_GHOST_COORDS32
-#define OLB_GHOST_COORDS32 0
+#define OLB_GHOST_COORDS32 1
 #endif
 // The pull step (two-buffer, state POST) of the paired kernel takes its populations
 // through TMA tile copies into shared memory (olb_tma.cuh) where the lattice fits;
@@ -523,6 +541,23 @@ __device__ __forceinline__ void collide(const Params<C>& p, C gamma, const C (&F
         cF -= F[d];
       }
     }
+    if (!TRT && OLB_FOLD_OMEGA_GENERIC) {
+      // omega (feq_k - f_k) with omega w_k folded into the equilibrium's coefficients
+      // (the products are common to the directions of equal weight):
+      //   Aw = omega w_k (drho - 1.5 rho u'^2), Bw = 4.5 omega w_k rho, Tw = 3 omega w_k rho
+      const C omw = om * wk;
+      const C symw = omw * (drho - rs) + (omw * C(4.5)) * rho * (cu * cu);
+      const C antiw = (omw * C(3)) * rho * cu;
+      f[kp] = (C(1) - om) * f[kp] + (symw + antiw);
+      f[k] = (C(1) - om) * f[k] + (symw - antiw);
+      if (p.forced) {
+        const C gs = gf * wk * (C(9) * cu * cF - C(3) * uF);
+        const C ga = gf * wk * C(3) * cF;
+        f[kp] += gs + ga;
+        f[k] += gs - ga;
+      }
+      continue;
+    }
     const C sym = wk * (drho + rho * (C(4.5) * cu * cu) - rs);
     const C anti = wk * C(3) * rho * cu;
     if (TRT) {
@@ -707,9 +742,8 @@ __device__ __forceinline__ bool on_edge(const Params<C>& p, int x, int y, int z)
 // fluid cell touches a non-periodic domain face) are recognised from the
 // coordinates, again without waiting for a load.
 template <class L, class S, int G, int SC, bool STATS, bool TRT>
-__global__ void __launch_bounds__(256, OLB_STEP_MIN_BLOCKS) k_step(Params<typename Store<S>::C> p,
-                                                                  const S* src, S* dst,
-                                                                  double* partials) {
+__global__ void __launch_bounds__(256, std::is_same<S, double>::value ? OLB_STEP64_MIN_BLOCKS : OLB_STEP_MIN_BLOCKS)
+    k_step(Params<typename Store<S>::C> p, const S* src, S* dst, double* partials) {
   using C = typename Store<S>::C;
   C sv[8] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
   const int tid = threadIdx.x;
