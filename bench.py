@@ -253,9 +253,13 @@ def variants(olb, torch):
         run_workload(lat, noise, 200)
         ms = time_step_kernel(torch, lat, 400)
         b = 19 * 2 * olb.STATE_ELEM[olb.DTYPES[dtype]]
-        out[f"cavity128_{dtype}_{scheme}"] = {
+        key = f"cavity128_{dtype}_{scheme}"
+        out[key] = {
             "MLUPS": round(fluid / ms / 1e3, 1), "bytes_per_update": b,
             "roofline_frac": round(fluid * b / (ms * 1e-3) / 1e9 / peak, 4)}
+        traffic = profiled_traffic(key, fluid)
+        if traffic is not None:
+            out[key]["traffic"] = round(traffic)  # DRAM bytes per launch (ncu), mean over the pattern's launches
         lat.close()
     # the same cavity with the TRT collision (magic parameter 3/16)
     for dtype in ("f32", "f16"):
@@ -264,9 +268,13 @@ def variants(olb, torch):
         run_workload(lat, noise, 200)
         ms = time_step_kernel(torch, lat, 400)
         b = 19 * 2 * olb.STATE_ELEM[olb.DTYPES[dtype]]
-        out[f"cavity128_{dtype}_pull_trt"] = {
+        key = f"cavity128_{dtype}_pull_trt"
+        out[key] = {
             "MLUPS": round(fluid / ms / 1e3, 1), "bytes_per_update": b,
             "roofline_frac": round(fluid * b / (ms * 1e-3) / 1e9 / peak, 4)}
+        traffic = profiled_traffic(key, fluid)
+        if traffic is not None:
+            out[key]["traffic"] = round(traffic)
         lat.close()
     # advection-diffusion, D3Q7 256^3 FP32, uniform velocity (7 x 4 x 2 = 56 B per update)
     try:
@@ -660,7 +668,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak_gbs()
     bytes_per_launch = fluid * 152
     achieved = bytes_per_launch / (kernel_ms * 1e-3) / 1e9
-    traffic = profiled_traffic("d3q19_f32_pull", fluid)
+    traffic = profiled_traffic("cavity128_f32_pull", fluid)
     e2e_units = fluid * LBM_STEPS * max(1, min(args.steps, 3)) * world
     extra = variants(olb, torch) if (args.variants and rank == 0) else None
     if world > 1:

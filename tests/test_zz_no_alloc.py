@@ -50,7 +50,12 @@ def _noalloc(olb, lat, f, material, force, stream):
 
 def _agree(a, b):
     assert abs(a[0] - b[0]) <= 1e-12 * abs(b[0])                      # mass
-    assert np.allclose(a[1:4], b[1:4], rtol=1e-9, atol=1e-15)         # momentum
+    # momentum: a component that cancels over the cells (a flow symmetric in it) is
+    # FP64 rounding noise whose value depends on the order of the sum, so it is
+    # compared on the scale of sum_x |j(x)|, which sqrt(sum rho * sum rho |u|^2)
+    # bounds (Cauchy-Schwarz; the energy is half the second sum)
+    scale = np.sqrt(2.0 * b[0] * b[4])
+    assert np.all(np.abs(a[1:4] - b[1:4]) <= 1e-9 * np.abs(b[1:4]) + 1e-13 * scale)
     assert abs(a[4] - b[4]) <= 1e-10 * abs(b[4])                      # energy
     assert abs(a[5] - b[5]) <= 1e-12 * abs(b[5])                      # max |u|
     assert a[6] == b[6] == 0
