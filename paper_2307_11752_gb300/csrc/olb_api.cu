@@ -318,8 +318,7 @@ struct olb_lattice {
   cudaStream_t stream = nullptr;
   DevBuf buf[2];
   int cur = 0, repr = PRE, scheme = OLB_PULL;
-  DevBuf mat, cls, wmask, pmask, word, plain, wall_u, gamma, ffield, partials, out8, err;
-  int plain_words = 0;  // 64-bit words per row of the plain-pair mask (0: nx odd, no mask)
+  DevBuf mat, cls, wmask, pmask, word, wall_u, gamma, ffield, partials, out8, err;
   bool outside_links = false;
   int y0 = 0, y1 = 0, z0 = 0, z1 = 0;  // bounding rows of the fluid cells
   std::vector<uint8_t> h_mat;
@@ -366,8 +365,6 @@ struct olb_lattice {
     p.ffield = has_ffield ? ffield.p : nullptr;
     p.pmask = static_cast<const uint32_t*>(pmask.p);
     p.word = static_cast<const uint32_t*>(word.p);
-    p.plain = plain_words ? static_cast<const unsigned long long*>(plain.p) : nullptr;
-    p.plain_words = plain_words;
     p.outside_links = outside_links ? 1 : 0;
     p.y0 = y0;
     p.y1 = y1;
@@ -749,7 +746,7 @@ const char* olb_last_error(void) { return g_err.c_str(); }
 #define OLB_STR(x) OLB_STR2(x)
 const char* olb_build_info(void) {
   return "sm_103a step_min_blocks=" OLB_STR(OLB_STEP_MIN_BLOCKS) " pair_min_blocks=" OLB_STR(OLB_PAIR_MIN_BLOCKS) " pair16_min_blocks=" OLB_STR(OLB_PAIR16_MIN_BLOCKS) " pair16_walls_min_blocks=" OLB_STR(OLB_PAIR16_WALLS_MIN_BLOCKS) " ghost16=" OLB_STR(OLB_GHOST_FIRST16) OLB_STR(OLB_GHOST_COORDS16) " ghost32=" OLB_STR(OLB_GHOST_FIRST32) OLB_STR(OLB_GHOST_COORDS32)
-         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " xwall_pairs=" OLB_STR(OLB_XWALL_PAIRS) " plain_mask=" OLB_STR(OLB_PLAIN_MASK) " fluid_box=" OLB_STR(OLB_FLUID_BOX) " pdl=" OLB_STR(OLB_PDL) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
+         " solid_fill=" OLB_STR(OLB_SOLID_FILL) " xwall_pairs=" OLB_STR(OLB_XWALL_PAIRS) " fluid_box=" OLB_STR(OLB_FLUID_BOX) " pdl=" OLB_STR(OLB_PDL) " plane_pad=" OLB_STR(OLB_PLANE_PAD)
 #ifdef OLB_NO_PAIRS
          " pairs=off"
 #else
@@ -796,15 +793,13 @@ int olb_lattice_create(olb_descriptor d, int nx, int ny, int nz, olb_dtype t, ol
   h->nz = nz;
   h->ncell = (int)cells;
   h->pitch = plane_pitch(cells);
-  h->plain_words = nx % 2 == 0 ? (nx / 2 + 63) / 64 : 0;
   std::memset(h->h_wall, 0, sizeof(h->h_wall));
   int rc;
   if ((rc = h->buf[0].reserve(h->state_bytes())) || (rc = h->mat.reserve(cells)) ||
       (rc = h->cls.reserve(cells)) || (rc = h->wmask.reserve(cells * 4)) || (rc = h->pmask.reserve(cells * 4)) ||
       (rc = h->word.reserve(cells * 4)) || (rc = h->err.reserve(sizeof(unsigned))) ||
       (rc = h->wall_u.reserve(sizeof(h->h_wall) + sizeof(h->h_wall_f))) ||
-      (rc = ensure_partials(h, h->grid_blocks())) ||
-      (h->plain_words && (rc = h->plain.reserve((size_t)ny * nz * h->plain_words * 8)))) {
+      (rc = ensure_partials(h, h->grid_blocks()))) {
     std::string msg = g_err;
     delete h;
     g_err = msg;
@@ -889,21 +884,6 @@ int olb_set_material(olb_handle h, const uint8_t* material, unsigned periodic_ma
   OLB_CUDA(cudaMemcpyAsync(h->wmask.p, wm.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "mask upload");
   OLB_CUDA(cudaMemcpyAsync(h->pmask.p, pm.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "mask upload");
   OLB_CUDA(cudaMemcpyAsync(h->word.p, wd.data(), n * 4, cudaMemcpyHostToDevice, h->stream), "word upload");
-  std::vector<unsigned long long> plain;
-  if (h->plain_words) {
-    // plain pairs: both cells fluid with no link of any kind (word == kWordFluid) and
-    // no link leaving the domain (class 3)
-    const int64_t rows = (int64_t)h->ny * h->nz;
-    plain.assign((size_t)rows * h->plain_words, 0ull);
-    for (int64_t r = 0; r < rows; ++r)
-      for (int pr = 0; pr < h->nx / 2; ++pr) {
-        const int64_t c = r * h->nx + 2 * pr;
-        if (wd[c] == kWordFluid && wd[c + 1] == kWordFluid && cls[c] != 3 && cls[c + 1] != 3)
-          plain[(size_t)(r * h->plain_words + (pr >> 6))] |= 1ull << (pr & 63);
-      }
-    OLB_CUDA(cudaMemcpyAsync(h->plain.p, plain.data(), plain.size() * 8, cudaMemcpyHostToDevice, h->stream),
-             "plain-pair mask upload");
-  }
   OLB_CUDA(cudaStreamSynchronize(h->stream), "material sync");
   h->h_mat.swap(m);
   h->periodic = periodic_mask;

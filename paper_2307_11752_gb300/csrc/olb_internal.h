@@ -45,12 +45,6 @@ struct HostParams {
   const void* ffield;     // per-cell force density [3][ncell] in the compute type, or nullptr
   const uint32_t* pmask;  // per cell: bit i set when x + c_i is a non-fluid cell of the lattice
   const uint32_t* word;   // per cell link word of the step kernel
-  // per row (z * ny + y) of the paired step kernel, plain_words 64-bit words: bit p
-  // set when pair p of the row (cells 2p, 2p + 1) is plain: both fluid, neither with
-  // a wall link, a moving link or a link leaving the domain (its words are both
-  // kWordFluid); nullptr when nx is odd
-  const unsigned long long* plain;
-  int plain_words;
   int outside_links;      // some fluid cell has a link leaving the domain
   int y0, y1, z0, z1;     // rows holding fluid cells: y in [y0, y1], z in [z0, z1]
   int az0, az1;           // active planes (a slab's interior): statistics count only these

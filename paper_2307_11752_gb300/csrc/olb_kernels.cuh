@@ -272,10 +272,6 @@ struct Params {
   const uint32_t* __restrict__ pmask;
   // per cell link word of the step kernel (see kWordFluid)
   const uint32_t* __restrict__ word;
-  // per row of the paired step kernel: bit p of word p / 64 set when pair p is
-  // plain (both words kWordFluid, no domain edge); null: load every word
-  const unsigned long long* __restrict__ plain;
-  int plain_words;
   int outside_links;  // some fluid cell has a link leaving the domain
   // step-kernel grid: gx * gy * nz tiles of (1 << tile_shift) x (256 >> tile_shift)
   int gx, gy, tile_shift;
@@ -312,8 +308,6 @@ Params<C> to_params(const HostParams& h) {
   p.gamma = reinterpret_cast<const C*>(h.gamma);
   p.pmask = h.pmask;
   p.word = h.word;
-  p.plain = h.plain;
-  p.plain_words = h.plain_words;
   p.outside_links = h.outside_links;
   p.y0 = h.y0;
   p.y1 = h.y1;

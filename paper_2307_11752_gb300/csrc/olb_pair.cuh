@@ -340,11 +340,6 @@ __device__ __forceinline__ int opaque(int v, float after) {
   return v;
 }
 
-// Per-row masks of the plain pairs (Params::plain) consulted before the link words.
-#ifndef OLB_PLAIN_MASK
-#define OLB_PLAIN_MASK 1
-#endif
-
 // Special store paths for pairs at walls on the x faces (see the store phase).
 #ifndef OLB_XWALL_PAIRS
 #define OLB_XWALL_PAIRS 1
@@ -654,19 +649,9 @@ __global__ void __launch_bounds__(256, TRT ? PairStore<S>::MIN_BLOCKS_TRT
     const int cell = n.cell();
     uint32_t w[2] = {kWordFluid, kWordFluid};
     if (WALLS) {
-      // a plain pair's words are both kWordFluid: its lane skips the word load (in a
-      // box-shaped domain only the pairs next to a wall load theirs)
-      bool plain = false;
-      if (OLB_PLAIN_MASK && p.plain) {
-        const int pair = x0 >> 1;
-        const unsigned long long m = p.plain[(size_t)(z * p.ny + y) * p.plain_words + (pair >> 6)];
-        plain = (m >> (pair & 63)) & 1ull;
-      }
-      if (!plain) {
-        const uint2 ww = *reinterpret_cast<const uint2*>(p.word + cell);
-        w[0] = ww.x;
-        w[1] = ww.y;
-      }
+      const uint2 ww = *reinterpret_cast<const uint2*>(p.word + cell);
+      w[0] = ww.x;
+      w[1] = ww.y;
     }
     F2 f[L::Q];
 #pragma unroll
