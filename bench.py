@@ -358,8 +358,8 @@ def experiment_adjoint384(torch, olb, fd_cells=64, h=1e-3, fd_slice=None):
     An FP64-storage adjoint does not fit at this size (the segment of 200 states
     alone would take 430 GB).
 
-    One FP64 forward run takes ~20 s here, so the 2 x 64 runs of the differences take
-    ~45 min: `fd_slice` = (a, b) differences only the seeded cells a .. b-1 (and tau
+    One FP64 forward run takes ~24 s on a GB300, so the 2 x 64 runs of the differences
+    take ~52 min: `fd_slice` = (a, b) differences only the seeded cells a .. b-1 (and tau
     only when a == 0), and the per-cell values are printed so that the slices of
     several runs can be put together."""
     nx, ny, nz, steps = 384, 192, 192, 4000
@@ -817,7 +817,12 @@ def main():
                "fd256": experiment_fd256}[args.experiment]
         kw = {}
         if args.fd_slice is not None:
-            kw["fd_slice"] = tuple(int(v) for v in args.fd_slice.split(":"))
+            if args.experiment != "adjoint384":
+                raise SystemExit("--fd-slice applies to --experiment adjoint384 only")
+            a, b = (int(v) for v in args.fd_slice.split(":"))
+            if not 0 <= a < b <= 64:
+                raise SystemExit(f"--fd-slice {args.fd_slice}: want 0 <= A < B <= 64")
+            kw["fd_slice"] = (a, b)
         print(json.dumps(run(torch, olb, **kw)), flush=True)
         return
     if args.impl == "reference":
