@@ -688,6 +688,8 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4),
                      "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "traffic": None if traffic is None else round(traffic),
+                     # DRAM bytes (ncu) over the same launch time: the HBM-only fraction
+                     "traffic_frac": None if traffic is None else round(traffic / (kernel_ms * 1e-3) / 1e9 / peak, 4),
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": round(kernel_ms, 5)},
         "e2e": {"value": round(e2e_units / e2e_max / 1e6, 2), "unit": "MLUPS",
