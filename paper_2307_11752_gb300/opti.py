@@ -117,8 +117,8 @@ def identify_porosity(evaluate: Callable, gamma_fixed, design, gamma_start, proj
 def identify_force(evaluate: Callable, force_fixed, design, force_start=0.0, iterations: int = 20,
                    history_size: int = 10, tolerance: float = 0.0, line_search_evaluations: int = 25) -> Result:
     """Minimise J(F) over the force density of the design cells: the control is the
-    distributed field, three components at each design cell (testFlowOpti3d with the
-    adjoint LBM).  No projection: the force is unconstrained.
+    distributed field, a force vector per design cell (testFlowOpti3d with the adjoint
+    LBM).  No projection: the force is unconstrained.
 
     evaluate     F (float64 tensor [3, nz, ny, nx]) -> 0-d tensor J, differentiable in F
                  (on the GPU: :func:`paper_2307_11752_gb300.olb.force_misfit_loss`)

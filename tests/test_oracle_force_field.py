@@ -1,6 +1,6 @@
 """Pins of the oracle's per-cell force field and of the adjoint gradient with
-respect to it (the distributed force control of the guide's testFlowOpti3d:
-"identify the force field ... three components at each mesh point").
+respect to it (the distributed force control of the guide's testFlowOpti3d, whose
+controls are the field's three components at every mesh point).
 
 * A field equal to the uniform force everywhere gives the uniform-force run.
 * A collision adds exactly the cell's force F(x) to its momentum (Guo, gamma = 1).
