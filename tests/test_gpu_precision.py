@@ -76,8 +76,9 @@ def test_storage_precision_tgv3d_64_5000_steps(olb, record_property):
     the strict ratio it reaches 7e-4 and 4e-4 at tau 0.51 and 0.52 but 1.2e-3 and
     3.0e-3 at tau 0.55 and 0.6, where the signal has decayed by up to exp(-4.8) and
     the ratio carries the random walk of 11-bit rounding over the mode's lifetime.
-    That is a miss against the benchmark spec's bound of 1e-3 relative at those two
-    tau, recorded as such; the test bounds the strict ratio at 5e-3."""
+    That misses the FP16 target of 1e-3 relative (Taylor-Green velocity error) at
+    those two tau, and is recorded as a miss; the test bounds the strict ratio at
+    5e-3."""
     import os
 
     import torch
