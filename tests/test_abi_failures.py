@@ -90,3 +90,31 @@ def test_oversized_lattices_are_rejected_before_allocation(lib):
     assert lib.olb_ade_create(olb.D3Q7, 1024, 1024, 512, olb.F32, ctypes.byref(h)) == -1
     assert "too large" in lib.olb_last_error().decode()
     assert h.value is None
+
+
+def test_every_handle_call_rejects_a_null_handle_on_the_host(lib):
+    """Every entry point that takes a lattice or scalar-lattice handle refuses NULL with
+    OLB_ERR_ARG and a message, before any device call (this runs without a GPU)."""
+    u3 = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    i64 = ctypes.c_int64()
+    i32 = ctypes.c_int()
+    calls = {
+        "olb_set_stream": (None, None), "olb_set_scheme": (None, 0),
+        "olb_set_material": (None, None, 0), "olb_set_wall_velocity": (None, 3, u3),
+        "olb_set_force": (None, u3), "olb_set_force_field": (None, None), "olb_set_porosity": (None, None),
+        "olb_init_equilibrium": (None, None, None), "olb_perturb_populations": (None, None),
+        "olb_set_populations": (None, None), "olb_get_populations": (None, None),
+        "olb_step_stats": (None, 1, None), "olb_moments": (None, None, None), "olb_diagnostics": (None, None),
+        "olb_adjoint_run": (None, 5, 2, None, None, None, None),
+        "olb_adjoint_gradients": (None, 5, 2, None, None, None, None),
+        "olb_synchronize": (None,), "olb_set_active_planes": (None, 1, 2),
+        "olb_halo_size": (None, ctypes.byref(i64), ctypes.byref(i32)),
+        "olb_halo_pack": (None, 0, None), "olb_halo_unpack": (None, 0, None),
+        "olb_inject_stalled_copy": (None, 0, 0), "olb_counters": (None, ctypes.byref(i64), ctypes.byref(i64)),
+        "olb_ade_set_stream": (None, None), "olb_ade_set_velocity": (None, u3, None),
+        "olb_ade_set_material": (None, None, 0, None), "olb_ade_set_velocity_from": (None, None),
+    }
+    for name, args in calls.items():
+        fn = getattr(lib, name)
+        assert fn(*args) == -1, name
+        assert lib.olb_last_error().decode(), name
