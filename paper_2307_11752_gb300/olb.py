@@ -423,19 +423,32 @@ class Lattice:
     def set_active_planes(self, z_first: int, z_last: int):
         _call("olb_set_active_planes", self.handle, int(z_first), int(z_last))
 
+    def halo_bytes(self) -> int:
+        """Bytes of one face's halo values (olb_halo_size)."""
+        n, e = ctypes.c_int64(), ctypes.c_int()
+        _call("olb_halo_size", self.handle, ctypes.byref(n), ctypes.byref(e))
+        return n.value * e.value
+
     def halo_buffer(self):
         """A device buffer (torch uint8 tensor) for one face's halo values."""
         import torch
 
-        n, e = ctypes.c_int64(), ctypes.c_int()
-        _call("olb_halo_size", self.handle, ctypes.byref(n), ctypes.byref(e))
-        return torch.empty(n.value * e.value, dtype=torch.uint8, device="cuda")
+        return torch.empty(self.halo_bytes(), dtype=torch.uint8, device="cuda")
+
+    def _halo_ptr(self, buf) -> int:
+        # the C call takes a bare pointer and cannot see the buffer's size
+        need = self.halo_bytes()
+        if not getattr(buf, "is_cuda", False) or not buf.is_contiguous():
+            raise ValueError("the halo buffer must be a contiguous CUDA tensor")
+        if buf.numel() * buf.element_size() < need:
+            raise ValueError(f"the halo buffer holds {buf.numel() * buf.element_size()} bytes, {need} needed")
+        return buf.data_ptr()
 
     def halo_pack(self, face: int, buf):
-        _call("olb_halo_pack", self.handle, int(face), buf.data_ptr())
+        _call("olb_halo_pack", self.handle, int(face), self._halo_ptr(buf))
 
     def halo_unpack(self, face: int, buf):
-        _call("olb_halo_unpack", self.handle, int(face), buf.data_ptr())
+        _call("olb_halo_unpack", self.handle, int(face), self._halo_ptr(buf))
 
     def synchronize(self):
         _call("olb_synchronize", self.handle)
