@@ -466,8 +466,10 @@ D2Q5, D3Q7 = 2, 3
 
 
 class AdeLattice:
-    """A passive scalar on a periodic D2Q5 / D3Q7 lattice (``olb_ade_*``): BGK towards
-    the first-order equilibrium, advected by a prescribed velocity."""
+    """A passive scalar on a D2Q5 / D3Q7 lattice (``olb_ade_*``): BGK towards the
+    first-order equilibrium, advected by a prescribed velocity or by a fluid
+    lattice's (``set_velocity_from``), with periodic axes, no-flux walls and Dirichlet
+    cells (``set_material``)."""
 
     def __init__(self, descriptor: int, shape, dtype: str = "f64", stream=None):
         import torch
